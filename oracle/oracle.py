@@ -1,0 +1,286 @@
+"""ctypes binding of the C oracle (salf_oracle.c).  Test infrastructure only."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "salf_oracle.c")
+_HDR = os.path.join(_HERE, "salf_oracle.h")
+_OUT = os.path.join(_HERE, "_build", "libsalf_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KIND = {"pinhole": 0, "fisheye": 1, "pano": 2, "lidar": 3, "explicit": 4}
+
+
+def library_path() -> str:
+    return _OUT
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no fast-math)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    stale = (not os.path.exists(_OUT) or
+             os.path.getmtime(_OUT) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _OUT + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class _SceneDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("origin", C.c_double * 3), ("s0", C.c_double),
+                ("dims", C.c_int32 * 3), ("max_level", C.c_int32), ("mode", C.c_int32),
+                ("level", C.c_void_p), ("ijk", C.c_void_p), ("params", C.c_void_p)]
+
+
+class _Sensor(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("fov", C.c_double), ("elev_min", C.c_double), ("elev_max", C.c_double),
+                ("pose0", C.c_double * 12), ("pose1", C.c_double * 12), ("t0", C.c_double),
+                ("t1", C.c_double), ("rolling_shutter", C.c_int32), ("t_near", C.c_double),
+                ("t_far", C.c_double), ("rays", C.c_void_p)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("t_min", C.c_double), ("background", C.c_double * 3),
+                ("want_intensity", C.c_int32), ("brute_force", C.c_int32)]
+
+
+class _Outputs(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("opacity", C.c_void_p),
+                ("intensity", C.c_void_p), ("t_end", C.c_void_p), ("term_gap", C.c_void_p),
+                ("n_visits", C.c_void_p), ("valid", C.c_void_p), ("visits", C.c_void_p),
+                ("visits_cap", C.c_int32)]
+
+
+class _Hit(C.Structure):
+    _fields_ = [("voxel", C.c_int32), ("t_in", C.c_double), ("t_out", C.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = C.CDLL(_OUT)
+            vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+            lib.orc_scene_create.argtypes = [C.POINTER(_SceneDesc), C.POINTER(vp)]
+            lib.orc_scene_create.restype = C.c_int
+            lib.orc_scene_free.argtypes = [vp]
+            lib.orc_scene_lookup.argtypes = [vp, i32, i32, i32, i32]
+            lib.orc_scene_lookup.restype = i64
+            lib.orc_gen_rays.argtypes = [C.POINTER(_Sensor), vp, i64, vp, vp, vp, vp, vp, vp]
+            lib.orc_pose_at.argtypes = [C.POINTER(_Sensor), dp, vp, vp]
+            lib.orc_sh_basis.argtypes = [vp, vp]
+            lib.orc_field.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+            lib.orc_trace.argtypes = [vp, vp, vp, dp, dp, i32, vp, i64]
+            lib.orc_trace.restype = i64
+            lib.orc_trace_eps.argtypes = [vp, vp, vp, dp, dp, dp, dp, i32, vp, i64]
+            lib.orc_trace_eps.restype = i64
+            lib.orc_render.argtypes = [vp, C.POINTER(_Sensor), C.POINTER(_Opts), vp, i64,
+                                       C.POINTER(_Outputs)]
+            lib.orc_backward.argtypes = [vp, C.POINTER(_Sensor), C.POINTER(_Opts), vp, i64, vp,
+                                         vp, vp, vp, vp]
+            lib.orc_num_threads.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+class OracleScene:
+    """A scene held by the oracle (FP64 copy of the records)."""
+
+    def __init__(self, scene, params=None):
+        lib = _load()
+        p = scene.params if params is None else params
+        self._level = np.ascontiguousarray(scene.level, dtype=np.uint8)
+        self._ijk = np.ascontiguousarray(scene.ijk, dtype=np.int32)
+        self._params = np.ascontiguousarray(p, dtype=np.float64)
+        self.n = int(self._level.shape[0])
+        self.mode = scene.mode
+        d = _SceneDesc()
+        d.n = self.n
+        d.origin[:] = [float(v) for v in scene.origin]
+        d.s0 = float(scene.s0)
+        d.dims[:] = [int(v) for v in scene.dims]
+        d.max_level = int(scene.max_level)
+        d.mode = 0 if scene.mode == "exp" else 1
+        d.level, d.ijk, d.params = _ptr(self._level), _ptr(self._ijk), _ptr(self._params)
+        h = C.c_void_p()
+        self.status = lib.orc_scene_create(C.byref(d), C.byref(h))
+        self._h = h if self.status == 0 else None
+
+    @property
+    def ok(self):
+        return self._h is not None
+
+    def close(self):
+        if self._h is not None:
+            _load().orc_scene_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lookup(self, level, i, j, k) -> int:
+        return int(_load().orc_scene_lookup(self._h, level, i, j, k))
+
+
+def _sensor(s):
+    c = _Sensor()
+    c.kind = KIND[s["kind"]]
+    c.width, c.height = int(s["width"]), int(s["height"])
+    c.fx, c.fy, c.cx, c.cy = (float(s[k]) for k in ("fx", "fy", "cx", "cy"))
+    c.fov, c.elev_min, c.elev_max = float(s["fov"]), float(s["elev_min"]), float(s["elev_max"])
+    c.pose0[:] = [float(v) for v in np.asarray(s["pose0"], dtype=np.float64).ravel()]
+    c.pose1[:] = [float(v) for v in np.asarray(s["pose1"], dtype=np.float64).ravel()]
+    c.t0, c.t1 = float(s["t0"]), float(s["t1"])
+    c.rolling_shutter = int(bool(s["rolling_shutter"]))
+    c.t_near, c.t_far = float(s["t_near"]), float(s["t_far"])
+    keep = None
+    if s["kind"] == "explicit":
+        keep = np.ascontiguousarray(s["rays"], dtype=np.float32)
+        c.rays = keep.ctypes.data
+    return c, keep
+
+
+def _opts(t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False, brute_force=False):
+    o = _Opts()
+    o.t_min = float(t_min)
+    o.background[:] = [float(v) for v in background]
+    o.want_intensity = int(bool(want_intensity))
+    o.brute_force = int(bool(brute_force))
+    return o
+
+
+def _idx(sensor, idx):
+    R = int(sensor["width"]) * int(sensor["height"])
+    if idx is None:
+        return None, R
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    assert idx.size == 0 or (idx.min() >= 0 and idx.max() < R)
+    return idx, int(idx.size)
+
+
+def gen_rays(sensor, idx=None):
+    lib = _load()
+    s, keep = _sensor(sensor)
+    idx, m = _idx(sensor, idx)
+    o = np.zeros((m, 3)); d = np.zeros((m, 3)); tn = np.zeros(m); tf = np.zeros(m)
+    tau = np.zeros(m); valid = np.zeros(m, np.uint8)
+    lib.orc_gen_rays(C.byref(s), _ptr(idx), m, _ptr(o), _ptr(d), _ptr(tn), _ptr(tf), _ptr(tau),
+                     _ptr(valid))
+    del keep
+    return dict(o=o, d=d, t_near=tn, t_far=tf, tau=tau, valid=valid.astype(bool))
+
+
+def pose_at(sensor, tau):
+    s, keep = _sensor(sensor)
+    R = np.zeros(9); t = np.zeros(3)
+    _load().orc_pose_at(C.byref(s), float(tau), _ptr(R), _ptr(t))
+    return R.reshape(3, 3), t
+
+
+def sh_basis(direction):
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    g = np.zeros(4)
+    _load().orc_sh_basis(_ptr(d), _ptr(g))
+    return g
+
+
+def field(record, mode, x, direction):
+    rec = np.ascontiguousarray(record, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    sig = np.zeros(1); c = np.zeros(3); io = np.zeros(1)
+    _load().orc_field(_ptr(rec), 0 if mode == "exp" else 1, _ptr(x), _ptr(d), _ptr(sig), _ptr(c),
+                      _ptr(io))
+    return float(sig[0]), c, float(io[0])
+
+
+def trace(oscene, o, d, t_near=0.0, t_far=np.inf, brute_force=False, cap=1 << 16):
+    """Hits of one ray: list of (voxel, t_in, t_out), sorted by entry."""
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    hits = (_Hit * cap)()
+    n = _load().orc_trace(oscene._h, _ptr(o), _ptr(d), float(t_near), float(t_far),
+                          int(bool(brute_force)), C.cast(hits, C.c_void_p), cap)
+    return [(hits[i].voxel, hits[i].t_in, hits[i].t_out) for i in range(min(n, cap))]
+
+
+def trace_eps(oscene, o, d, t_near, t_far, eps_abs, eps_rel, sign, cap=1 << 16):
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    ids = np.zeros(cap, np.int32)
+    n = _load().orc_trace_eps(oscene._h, _ptr(o), _ptr(d), float(t_near), float(t_far),
+                              float(eps_abs), float(eps_rel), int(sign), _ptr(ids), cap)
+    return ids[:min(n, cap)].tolist()
+
+
+def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
+           want_intensity=False, brute_force=False, visits_cap=0):
+    """Render the selected rays (all if idx is None) in FP64."""
+    lib = _load()
+    s, keep = _sensor(sensor)
+    idx, m = _idx(sensor, idx)
+    o = _Outputs()
+    res = dict(rgb=np.zeros((m, 3)), depth=np.zeros(m), opacity=np.zeros(m),
+               intensity=np.zeros(m), t_end=np.zeros(m), term_gap=np.zeros(m),
+               n_visits=np.zeros(m, np.int32), valid=np.zeros(m, np.uint8))
+    for k, v in res.items():
+        setattr(o, k, _ptr(v))
+    if visits_cap > 0:
+        res["visits"] = np.full((m, visits_cap), -1, np.int32)
+        o.visits = _ptr(res["visits"])
+        o.visits_cap = int(visits_cap)
+    opt = _opts(t_min, background, want_intensity, brute_force)
+    st = lib.orc_render(oscene._h, C.byref(s), C.byref(opt), _ptr(idx), m, C.byref(o))
+    if st != 0:
+        raise RuntimeError(f"oracle render failed: {st}")
+    del keep
+    res["valid"] = res["valid"].astype(bool)
+    return res
+
+
+def backward(oscene, sensor, g_rgb=None, g_depth=None, g_opacity=None, g_intensity=None,
+             idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
+             brute_force=False):
+    """Gradient (n, 32) of sum(g . outputs) w.r.t. every record scalar."""
+    lib = _load()
+    s, keep = _sensor(sensor)
+    idx, m = _idx(sensor, idx)
+    grad = np.zeros((oscene.n, 32))
+
+    def arr(a, shape):
+        if a is None:
+            return None
+        return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+    gr, gd, go, gi = arr(g_rgb, (m, 3)), arr(g_depth, (m,)), arr(g_opacity, (m,)), arr(g_intensity, (m,))
+    opt = _opts(t_min, background, want_intensity, brute_force)
+    st = lib.orc_backward(oscene._h, C.byref(s), C.byref(opt), _ptr(idx), m, _ptr(gr), _ptr(gd),
+                          _ptr(go), _ptr(gi), _ptr(grad))
+    if st != 0:
+        raise RuntimeError(f"oracle backward failed: {st}")
+    del keep
+    return grad

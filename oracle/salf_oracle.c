@@ -1,0 +1,831 @@
+/*
+ * salf_oracle.c -- FP64 CPU oracle for SaLF ray-cast rendering.
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, smoke check and the benchmark's CPU
+ * baseline).  Plain and slow on purpose: every step is the definition written
+ * out, in the order the paper states it.
+ *
+ * Readings of points the paper leaves open (all shared with the docs):
+ *   - gamma(omega), Eq. 2: real spherical harmonics of bands l <= 1, 4 values
+ *     [C0, C1*w_y, C1*w_z, C1*w_x], C0 = 1/(2 sqrt(pi)), C1 = sqrt(3)/(2 sqrt(pi)),
+ *     no Condon-Shortley sign; omega = the unit ray direction (world frame).
+ *   - local coordinates x = (X - voxel centre) / (edge / 2) in [-1, 1]^3,
+ *     voxel frames = world frame (rotation q fixed at identity, Sec. III-A).
+ *   - Eq. 2 uses x (not the homogeneous x-hat): no colour bias besides SH.
+ *   - sampling point (Sec. III-A, after Eq. 4): midpoint of the ray-voxel
+ *     segment clipped to [t_near, t_far]; delta = the clipped length.
+ *   - a voxel is hit iff that clipped length is > 0; in FP64 "> 0" is read as
+ *     "> 1e-9 finest-cell edges", so that rays passing exactly through a
+ *     voxel edge or corner (length 0 in exact arithmetic, ~1e-15 after
+ *     rounding) count as misses whichever way the rounding goes.
+ *   - Eq. 6 with sign(0) = 0.
+ *   - depth = sum_i w_i t_mid,i (unnormalised), opacity = sum_i w_i,
+ *     intensity = sum_i w_i sigmoid(W_int . x-hat); colour premultiplied,
+ *     plus T_end * background.
+ *   - early termination: composite voxel i, then stop if T_{i+1} < t_min.
+ *   - sensor conventions: see the sensor section below.
+ */
+#include "salf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define REC 32
+
+typedef struct {
+  int32_t l, i, j, k, idx;
+} okey;
+
+struct orc_scene {
+  int64_t n;
+  double origin[3];
+  double s0;
+  int32_t dims[3];
+  int32_t K;
+  int32_t mode;
+  double min_len; /* hit threshold on the clipped segment length */
+  uint8_t* level;
+  int32_t* ijk;
+  double* params;
+  okey* keys; /* sorted by (l, k, j, i) */
+};
+
+static int key_cmp(const void* pa, const void* pb) {
+  const okey* a = (const okey*)pa;
+  const okey* b = (const okey*)pb;
+  if (a->l != b->l) return a->l < b->l ? -1 : 1;
+  if (a->k != b->k) return a->k < b->k ? -1 : 1;
+  if (a->j != b->j) return a->j < b->j ? -1 : 1;
+  if (a->i != b->i) return a->i < b->i ? -1 : 1;
+  return 0;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+int64_t orc_scene_lookup(const orc_scene* s, int32_t level, int32_t i, int32_t j, int32_t k) {
+  okey q = {level, i, j, k, -1};
+  const okey* f = (const okey*)bsearch(&q, s->keys, (size_t)s->n, sizeof(okey), key_cmp);
+  return f ? f->idx : -1;
+}
+
+void orc_scene_free(orc_scene* s) {
+  if (!s) return;
+  free(s->level);
+  free(s->ijk);
+  free(s->params);
+  free(s->keys);
+  free(s);
+}
+
+/* Sec. III-A: voxels live on the level grids of a root grid; Sec. III-D:
+ * voxels are disjoint, so a voxel whose ancestor (or itself) is present
+ * again is rejected. */
+int orc_scene_create(const orc_scene_desc* d, orc_scene** out) {
+  *out = NULL;
+  if (d->n < 0 || d->max_level < 0 || d->max_level > 16 || d->s0 <= 0) return 1;
+  for (int a = 0; a < 3; ++a)
+    if (d->dims[a] <= 0) return 1;
+  orc_scene* s = (orc_scene*)calloc(1, sizeof(orc_scene));
+  s->n = d->n;
+  memcpy(s->origin, d->origin, sizeof(s->origin));
+  s->s0 = d->s0;
+  memcpy(s->dims, d->dims, sizeof(s->dims));
+  s->K = d->max_level;
+  s->mode = d->mode;
+  s->min_len = 1e-9 * d->s0 / (double)(1 << d->max_level);
+  size_t n = (size_t)d->n;
+  s->level = (uint8_t*)malloc(n ? n : 1);
+  s->ijk = (int32_t*)malloc((n ? n : 1) * 3 * sizeof(int32_t));
+  s->params = (double*)malloc((n ? n : 1) * REC * sizeof(double));
+  s->keys = (okey*)malloc((n ? n : 1) * sizeof(okey));
+  if (n) {
+    memcpy(s->level, d->level, n);
+    memcpy(s->ijk, d->ijk, n * 3 * sizeof(int32_t));
+    memcpy(s->params, d->params, n * REC * sizeof(double));
+  }
+  for (size_t v = 0; v < n; ++v) {
+    int32_t l = s->level[v];
+    if (l > s->K) { orc_scene_free(s); return 1; }
+    for (int a = 0; a < 3; ++a) {
+      int64_t lim = (int64_t)s->dims[a] << l;
+      if (s->ijk[3 * v + a] < 0 || s->ijk[3 * v + a] >= lim) { orc_scene_free(s); return 1; }
+    }
+    if (s->mode == 1 && !(s->params[REC * v + 25] > 0 && s->params[REC * v + 26] > 0)) {
+      orc_scene_free(s);
+      return 1;
+    }
+    okey kk = {l, s->ijk[3 * v], s->ijk[3 * v + 1], s->ijk[3 * v + 2], (int32_t)v};
+    s->keys[v] = kk;
+  }
+  qsort(s->keys, n, sizeof(okey), key_cmp);
+  for (size_t v = 1; v < n; ++v)
+    if (key_cmp(&s->keys[v - 1], &s->keys[v]) == 0) { orc_scene_free(s); return 4; }
+  for (size_t v = 0; v < n; ++v) {
+    int32_t l = s->level[v];
+    for (int32_t la = 0; la < l; ++la) {
+      int sh = l - la;
+      if (orc_scene_lookup(s, la, s->ijk[3 * v] >> sh, s->ijk[3 * v + 1] >> sh,
+                           s->ijk[3 * v + 2] >> sh) >= 0) {
+        orc_scene_free(s);
+        return 4;
+      }
+    }
+  }
+  *out = s;
+  return 0;
+}
+
+static void voxel_box(const orc_scene* s, int64_t v, double lo[3], double hi[3], double* edge) {
+  int32_t l = s->level[v];
+  double e = s->s0 / (double)(1 << l);
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = s->origin[a] + (double)s->ijk[3 * v + a] * e;
+    hi[a] = lo[a] + e;
+  }
+  *edge = e;
+}
+
+/* Ray-box slab test: parameter interval where o + t d is inside [lo, hi). */
+static int slab(const double lo[3], const double hi[3], const double o[3], const double d[3],
+                double* t0, double* t1) {
+  double a = -INFINITY, b = INFINITY;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (d[ax] != 0.0) {
+      double ta = (lo[ax] - o[ax]) / d[ax];
+      double tb = (hi[ax] - o[ax]) / d[ax];
+      if (ta > tb) { double t = ta; ta = tb; tb = t; }
+      if (ta > a) a = ta;
+      if (tb < b) b = tb;
+    } else if (o[ax] < lo[ax] || o[ax] >= hi[ax]) {
+      return 0;
+    }
+  }
+  *t0 = a;
+  *t1 = b;
+  return 1;
+}
+
+static double dmax(double a, double b) { return a > b ? a : b; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+
+typedef struct {
+  orc_hit* h;
+  int64_t n, cap;
+} hitvec;
+
+static void hv_push(hitvec* v, int32_t vox, double a, double b) {
+  if (v->n == v->cap) {
+    v->cap = v->cap ? 2 * v->cap : 64;
+    v->h = (orc_hit*)realloc(v->h, (size_t)v->cap * sizeof(orc_hit));
+  }
+  v->h[v->n].voxel = vox;
+  v->h[v->n].t_in = a;
+  v->h[v->n].t_out = b;
+  v->n++;
+}
+
+typedef struct {
+  double key;
+  orc_hit h;
+} skey;
+
+static int skey_cmp(const void* pa, const void* pb) {
+  const skey* a = (const skey*)pa;
+  const skey* b = (const skey*)pb;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return a->h.voxel < b->h.voxel ? -1 : (a->h.voxel > b->h.voxel);
+}
+
+/* Order hits by their clipped entry distance max(t_in, tn). */
+static void sort_hits(hitvec* v, double tn) {
+  if (v->n < 2) return;
+  skey* k = (skey*)malloc((size_t)v->n * sizeof(skey));
+  for (int64_t i = 0; i < v->n; ++i) {
+    k[i].key = dmax(v->h[i].t_in, tn);
+    k[i].h = v->h[i];
+  }
+  qsort(k, (size_t)v->n, sizeof(skey), skey_cmp);
+  for (int64_t i = 0; i < v->n; ++i) v->h[i] = k[i].h;
+  free(k);
+}
+
+static int32_t owner_of_fine_cell(const orc_scene* s, const int64_t c[3]) {
+  for (int32_t l = 0; l <= s->K; ++l) {
+    int sh = s->K - l;
+    int64_t v = orc_scene_lookup(s, l, (int32_t)(c[0] >> sh), (int32_t)(c[1] >> sh),
+                                 (int32_t)(c[2] >> sh));
+    if (v >= 0) return (int32_t)v;
+  }
+  return -1;
+}
+
+static int i32_cmp(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return x < y ? -1 : (x > y);
+}
+
+typedef struct {
+  int32_t* v;
+  int64_t n, cap;
+} ivec;
+
+static void iv_push(ivec* v, int32_t x) {
+  if (v->n == v->cap) {
+    v->cap = v->cap ? 2 * v->cap : 64;
+    v->v = (int32_t*)realloc(v->v, (size_t)v->cap * sizeof(int32_t));
+  }
+  v->v[v->n++] = x;
+}
+
+/* Candidate voxels: owners of the finest-level cells the ray passes through
+ * (Amanatides-Woo grid walk), optionally with their 26 neighbours.  This only
+ * enumerates candidates; which of them are hit is decided by the slab test. */
+static void dda_candidates(const orc_scene* s, const double o[3], const double d[3], double tn,
+                           double tf, int neighbours, ivec* cand) {
+  int64_t Gf[3];
+  double sf = s->s0 / (double)(1 << s->K);
+  double lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    Gf[a] = (int64_t)s->dims[a] << s->K;
+    lo[a] = s->origin[a];
+    hi[a] = s->origin[a] + (double)s->dims[a] * s->s0;
+  }
+  double ra, rb;
+  if (!slab(lo, hi, o, d, &ra, &rb)) return;
+  double ta = dmax(ra, tn), tb = dmin(rb, tf);
+  if (!(ta < tb)) return;
+  int64_t c[3], step[3];
+  double tmax[3], tdel[3];
+  for (int a = 0; a < 3; ++a) {
+    double p = o[a] + ta * d[a];
+    int64_t ci = (int64_t)floor((p - s->origin[a]) / sf);
+    if (ci < 0) ci = 0;
+    if (ci >= Gf[a]) ci = Gf[a] - 1;
+    c[a] = ci;
+    if (d[a] > 0) {
+      step[a] = 1;
+      tmax[a] = (s->origin[a] + (double)(ci + 1) * sf - o[a]) / d[a];
+      tdel[a] = sf / d[a];
+    } else if (d[a] < 0) {
+      step[a] = -1;
+      tmax[a] = (s->origin[a] + (double)ci * sf - o[a]) / d[a];
+      tdel[a] = -sf / d[a];
+    } else {
+      step[a] = 0;
+      tmax[a] = INFINITY;
+      tdel[a] = INFINITY;
+    }
+  }
+  int32_t last = -2;
+  for (;;) {
+    if (neighbours) {
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int64_t q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+            if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= Gf[0] || q[1] >= Gf[1] ||
+                q[2] >= Gf[2])
+              continue;
+            int32_t w = owner_of_fine_cell(s, q);
+            if (w >= 0) iv_push(cand, w);
+          }
+    } else {
+      int32_t w = owner_of_fine_cell(s, c);
+      if (w >= 0 && w != last) iv_push(cand, w);
+      last = w;
+    }
+    int a = 0;
+    if (tmax[1] < tmax[a]) a = 1;
+    if (tmax[2] < tmax[a]) a = 2;
+    if (!(tmax[a] < tb)) break;
+    c[a] += step[a];
+    tmax[a] += tdel[a];
+    if (c[a] < 0 || c[a] >= Gf[a]) break;
+  }
+}
+
+static void unique_ids(ivec* v) {
+  if (v->n < 2) return;
+  qsort(v->v, (size_t)v->n, sizeof(int32_t), i32_cmp);
+  int64_t w = 1;
+  for (int64_t i = 1; i < v->n; ++i)
+    if (v->v[i] != v->v[w - 1]) v->v[w++] = v->v[i];
+  v->n = w;
+}
+
+static void trace_vec(const orc_scene* s, const double o[3], const double d[3], double tn,
+                      double tf, int32_t brute, hitvec* out) {
+  double lo[3], hi[3], e, a, b;
+  out->n = 0;
+  if (brute) {
+    for (int64_t v = 0; v < s->n; ++v) {
+      voxel_box(s, v, lo, hi, &e);
+      if (slab(lo, hi, o, d, &a, &b) && dmin(b, tf) - dmax(a, tn) > s->min_len)
+        hv_push(out, (int32_t)v, a, b);
+    }
+  } else {
+    ivec cand = {0, 0, 0};
+    dda_candidates(s, o, d, tn, tf, 0, &cand);
+    unique_ids(&cand);
+    for (int64_t i = 0; i < cand.n; ++i) {
+      int32_t v = cand.v[i];
+      voxel_box(s, v, lo, hi, &e);
+      if (slab(lo, hi, o, d, &a, &b) && dmin(b, tf) - dmax(a, tn) > s->min_len)
+        hv_push(out, v, a, b);
+    }
+    free(cand.v);
+  }
+  sort_hits(out, tn);
+}
+
+int64_t orc_trace(const orc_scene* s, const double o[3], const double d[3], double tn, double tf,
+                  int32_t brute_force, orc_hit* hits, int64_t cap) {
+  hitvec hv = {0, 0, 0};
+  trace_vec(s, o, d, tn, tf, brute_force, &hv);
+  for (int64_t i = 0; i < hv.n && i < cap; ++i) hits[i] = hv.h[i];
+  int64_t n = hv.n;
+  free(hv.h);
+  return n;
+}
+
+int64_t orc_trace_eps(const orc_scene* s, const double o[3], const double d[3], double tn,
+                      double tf, double eps_abs, double eps_rel, int32_t sign, int32_t* ids,
+                      int64_t cap) {
+  ivec cand = {0, 0, 0};
+  if (s->n <= 20000) {
+    for (int64_t v = 0; v < s->n; ++v) iv_push(&cand, (int32_t)v);
+  } else {
+    dda_candidates(s, o, d, tn, tf, 1, &cand);
+    unique_ids(&cand);
+  }
+  hitvec hv = {0, 0, 0};
+  for (int64_t i = 0; i < cand.n; ++i) {
+    int32_t v = cand.v[i];
+    double lo[3], hi[3], e, a, b, dist = 0;
+    voxel_box(s, v, lo, hi, &e);
+    for (int ax = 0; ax < 3; ++ax) {
+      double cc = 0.5 * (lo[ax] + hi[ax]) - o[ax];
+      dist += cc * cc;
+    }
+    double eps = eps_abs + eps_rel * sqrt(dist);
+    for (int ax = 0; ax < 3; ++ax) {
+      lo[ax] -= sign * eps;
+      hi[ax] += sign * eps;
+    }
+    if (slab(lo, hi, o, d, &a, &b) && dmin(b, tf) - dmax(a, tn) > s->min_len)
+      hv_push(&hv, v, a, b);
+  }
+  sort_hits(&hv, tn);
+  for (int64_t i = 0; i < hv.n && i < cap; ++i) ids[i] = hv.h[i].voxel;
+  int64_t n = hv.n;
+  free(hv.h);
+  free(cand.v);
+  return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sensors (Fig. 2, Sec. V-C).  Camera frame: x right, y down, z forward.    */
+/* LiDAR frame: x forward, y left, z up.                                     */
+/* ------------------------------------------------------------------------ */
+
+static void mat_to_quat(const double* P, double q[4]) {
+  /* rotation part of a row-major 3x4 [R|t]; q = (w, x, y, z); Shoemake. */
+  double r00 = P[0], r01 = P[1], r02 = P[2];
+  double r10 = P[4], r11 = P[5], r12 = P[6];
+  double r20 = P[8], r21 = P[9], r22 = P[10];
+  double tr = r00 + r11 + r22, S;
+  if (tr > 0) {
+    S = sqrt(tr + 1.0) * 2.0;
+    q[0] = 0.25 * S;
+    q[1] = (r21 - r12) / S;
+    q[2] = (r02 - r20) / S;
+    q[3] = (r10 - r01) / S;
+  } else if (r00 > r11 && r00 > r22) {
+    S = sqrt(1.0 + r00 - r11 - r22) * 2.0;
+    q[0] = (r21 - r12) / S;
+    q[1] = 0.25 * S;
+    q[2] = (r01 + r10) / S;
+    q[3] = (r02 + r20) / S;
+  } else if (r11 > r22) {
+    S = sqrt(1.0 + r11 - r00 - r22) * 2.0;
+    q[0] = (r02 - r20) / S;
+    q[1] = (r01 + r10) / S;
+    q[2] = 0.25 * S;
+    q[3] = (r12 + r21) / S;
+  } else {
+    S = sqrt(1.0 + r22 - r00 - r11) * 2.0;
+    q[0] = (r10 - r01) / S;
+    q[1] = (r02 + r20) / S;
+    q[2] = (r12 + r21) / S;
+    q[3] = 0.25 * S;
+  }
+}
+
+static void quat_to_mat(const double q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z);
+  R[1] = 2 * (x * y - w * z);
+  R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);
+  R[4] = 1 - 2 * (x * x + z * z);
+  R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);
+  R[7] = 2 * (y * z + w * x);
+  R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Pose at time tau: linear translation, spherical-linear rotation between
+ * pose0 (t0) and pose1 (t1).  At the start time the pose is pose0 itself. */
+void orc_pose_at(const orc_sensor* sen, double tau, double R[9], double t[3]) {
+  double s = 0.0;
+  if (sen->t1 > sen->t0) s = (tau - sen->t0) / (sen->t1 - sen->t0);
+  if (s == 0.0) {
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) R[3 * r + c] = sen->pose0[4 * r + c];
+      t[r] = sen->pose0[4 * r + 3];
+    }
+    return;
+  }
+  double q0[4], q1[4], q[4];
+  mat_to_quat(sen->pose0, q0);
+  mat_to_quat(sen->pose1, q1);
+  double dot = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2] + q0[3] * q1[3];
+  if (dot < 0) {
+    dot = -dot;
+    for (int i = 0; i < 4; ++i) q1[i] = -q1[i];
+  }
+  if (dot > 0.9999999) {
+    double nn = 0;
+    for (int i = 0; i < 4; ++i) {
+      q[i] = (1 - s) * q0[i] + s * q1[i];
+      nn += q[i] * q[i];
+    }
+    nn = sqrt(nn);
+    for (int i = 0; i < 4; ++i) q[i] /= nn;
+  } else {
+    double th = acos(dot), st = sin(th);
+    double a = sin((1 - s) * th) / st, b = sin(s * th) / st;
+    for (int i = 0; i < 4; ++i) q[i] = a * q0[i] + b * q1[i];
+  }
+  quat_to_mat(q, R);
+  for (int r = 0; r < 3; ++r) t[r] = (1 - s) * sen->pose0[4 * r + 3] + s * sen->pose1[4 * r + 3];
+}
+
+static void one_ray(const orc_sensor* sen, int64_t r, double o[3], double d[3], double* tn,
+                    double* tf, double* tau, uint8_t* valid) {
+  const int64_t W = sen->width, H = sen->height;
+  *valid = 1;
+  if (sen->kind == 4) {
+    const float* q = sen->rays + 8 * r;
+    double nn = 0;
+    for (int a = 0; a < 3; ++a) {
+      o[a] = q[a];
+      d[a] = q[3 + a];
+      nn += d[a] * d[a];
+    }
+    nn = sqrt(nn);
+    for (int a = 0; a < 3; ++a) d[a] /= nn;
+    *tn = q[6];
+    *tf = q[7] > 0 ? (double)q[7] : INFINITY;
+    *tau = 0;
+    if (!(nn > 0)) *valid = 0;
+    return;
+  }
+  int64_t u = r % W, v = r / W;
+  double ds[3];
+  if (sen->kind == 3) {
+    /* spinning LiDAR: row v = beam (row 0 highest), column u = azimuth */
+    double e = sen->elev_max;
+    if (H > 1) e = sen->elev_max - (double)v * (sen->elev_max - sen->elev_min) / (double)(H - 1);
+    double ph = 2.0 * M_PI * (double)u / (double)W;
+    ds[0] = cos(e) * cos(ph);
+    ds[1] = cos(e) * sin(ph);
+    ds[2] = sin(e);
+    *tau = sen->t0 + ((double)u / (double)W) * (sen->t1 - sen->t0);
+  } else {
+    double px = (double)u + 0.5, py = (double)v + 0.5;
+    if (sen->kind == 0) {
+      ds[0] = (px - sen->cx) / sen->fx;
+      ds[1] = (py - sen->cy) / sen->fy;
+      ds[2] = 1.0;
+    } else if (sen->kind == 1) {
+      /* equidistant: image radius = f * theta */
+      double mx = (px - sen->cx) / sen->fx, my = (py - sen->cy) / sen->fy;
+      double th = sqrt(mx * mx + my * my);
+      if (th > 0.5 * sen->fov) *valid = 0;
+      if (th > 0) {
+        ds[0] = sin(th) * mx / th;
+        ds[1] = sin(th) * my / th;
+      } else {
+        ds[0] = ds[1] = 0;
+      }
+      ds[2] = cos(th);
+    } else {
+      /* equirectangular: longitude across the width (0 at the centre column,
+       * increasing to the right), latitude from elev_max (top) to elev_min */
+      double lon = 2.0 * M_PI * (px / (double)W - 0.5);
+      double lat = sen->elev_max - (py / (double)H) * (sen->elev_max - sen->elev_min);
+      ds[0] = cos(lat) * sin(lon);
+      ds[1] = -sin(lat);
+      ds[2] = cos(lat) * cos(lon);
+    }
+    *tau = sen->t0;
+    if (sen->rolling_shutter && H > 1)
+      *tau = sen->t0 + ((double)v / (double)(H - 1)) * (sen->t1 - sen->t0);
+  }
+  double R[9], t[3];
+  orc_pose_at(sen, *tau, R, t);
+  double nn = 0;
+  for (int a = 0; a < 3; ++a) {
+    d[a] = R[3 * a] * ds[0] + R[3 * a + 1] * ds[1] + R[3 * a + 2] * ds[2];
+    nn += d[a] * d[a];
+    o[a] = t[a];
+  }
+  nn = sqrt(nn);
+  for (int a = 0; a < 3; ++a) d[a] /= nn;
+  *tn = sen->t_near;
+  *tf = sen->t_far > 0 ? sen->t_far : INFINITY;
+}
+
+int orc_gen_rays(const orc_sensor* sen, const int64_t* idx, int64_t m, double* o, double* d,
+                 double* tn, double* tf, double* tau, uint8_t* valid) {
+  if (sen->width <= 0 || sen->height <= 0) return 1;
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t r = idx ? idx[i] : i;
+    one_ray(sen, r, o + 3 * i, d + 3 * i, tn + i, tf + i, tau + i, valid + i);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Local fields (Eq. 1, 2, 5, 6)                                             */
+/* ------------------------------------------------------------------------ */
+
+void orc_sh_basis(const double dir[3], double g[4]) {
+  const double C0 = 0.5 / sqrt(M_PI);
+  const double C1 = 0.5 * sqrt(3.0 / M_PI);
+  g[0] = C0;
+  g[1] = C1 * dir[1];
+  g[2] = C1 * dir[2];
+  g[3] = C1 * dir[0];
+}
+
+static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+static double sgn(double x) { return (x > 0) - (x < 0); }
+
+void orc_field(const double* rec, int32_t mode, const double x[3], const double dir[3],
+               double* sigma, double c[3], double* iota) {
+  double xh[4] = {x[0], x[1], x[2], 1.0};
+  double g[4];
+  orc_sh_basis(dir, g);
+  double lin = 0;
+  for (int a = 0; a < 4; ++a) lin += rec[a] * xh[a];
+  if (mode == 0) {
+    *sigma = exp(lin); /* Eq. 1 */
+  } else {
+    double a = rec[25], b = rec[26]; /* Eq. 5 gives lin = s_pm; Eq. 6 */
+    *sigma = 0.5 * a + 0.5 * a * sgn(lin) * (1.0 - exp(-fabs(lin) / b));
+  }
+  for (int r = 0; r < 3; ++r) { /* Eq. 2 */
+    double z = 0;
+    for (int a = 0; a < 3; ++a) z += rec[4 + 3 * r + a] * x[a];
+    for (int k = 0; k < 4; ++k) z += rec[13 + 4 * r + k] * g[k];
+    c[r] = sigmoid(z);
+  }
+  double zi = 0;
+  for (int a = 0; a < 4; ++a) zi += rec[27 + a] * xh[a];
+  *iota = sigmoid(zi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rendering (Eq. 3-4)                                                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t n;            /* composited voxels */
+  int32_t* vox;
+  double *tm, *dl, *sig, *lin, *c, *io, *alpha, *T, *w, *x;
+  double t_end, gap;
+} ray_record;
+
+static void rr_free(ray_record* rr) {
+  free(rr->vox);
+  free(rr->tm);
+  free(rr->dl);
+  free(rr->sig);
+  free(rr->lin);
+  free(rr->c);
+  free(rr->io);
+  free(rr->alpha);
+  free(rr->T);
+  free(rr->w);
+  free(rr->x);
+}
+
+/* Trace one ray and composite front to back; keeps every per-voxel quantity
+ * so that the adjoint can be written as plain sums. */
+static void composite_ray(const orc_scene* s, const orc_opts* opt, const double o[3],
+                          const double d[3], double tn, double tf, ray_record* rr) {
+  hitvec hv = {0, 0, 0};
+  trace_vec(s, o, d, tn, tf, opt->brute_force, &hv);
+  int64_t m = hv.n;
+  size_t M = (size_t)(m ? m : 1);
+  rr->vox = (int32_t*)malloc(M * sizeof(int32_t));
+  rr->tm = (double*)malloc(M * sizeof(double));
+  rr->dl = (double*)malloc(M * sizeof(double));
+  rr->sig = (double*)malloc(M * sizeof(double));
+  rr->lin = (double*)malloc(M * sizeof(double));
+  rr->c = (double*)malloc(3 * M * sizeof(double));
+  rr->io = (double*)malloc(M * sizeof(double));
+  rr->alpha = (double*)malloc(M * sizeof(double));
+  rr->T = (double*)malloc(M * sizeof(double));
+  rr->w = (double*)malloc(M * sizeof(double));
+  rr->x = (double*)malloc(3 * M * sizeof(double));
+  double T = 1.0, gap = INFINITY;
+  int64_t k = 0;
+  for (; k < m; ++k) {
+    int32_t v = hv.h[k].voxel;
+    double lo[3], hi[3], e;
+    voxel_box(s, v, lo, hi, &e);
+    double a = dmax(hv.h[k].t_in, tn), b = dmin(hv.h[k].t_out, tf);
+    double tm = 0.5 * (a + b), dl = b - a;
+    double x[3];
+    for (int ax = 0; ax < 3; ++ax) {
+      double X = o[ax] + tm * d[ax];
+      double ctr = 0.5 * (lo[ax] + hi[ax]);
+      x[ax] = (X - ctr) / (0.5 * e);
+    }
+    const double* rec = s->params + (size_t)REC * v;
+    double sig, c[3], io;
+    orc_field(rec, s->mode, x, d, &sig, c, &io);
+    if (!opt->want_intensity) io = 0.0;
+    double lin = 0;
+    for (int q = 0; q < 3; ++q) lin += rec[q] * x[q];
+    lin += rec[3];
+    double alpha = 1.0 - exp(-sig * dl); /* Eq. 4 */
+    double w = T * alpha;                /* Eq. 3 weight T_i alpha_i */
+    rr->vox[k] = v;
+    rr->tm[k] = tm;
+    rr->dl[k] = dl;
+    rr->sig[k] = sig;
+    rr->lin[k] = lin;
+    for (int q = 0; q < 3; ++q) {
+      rr->c[3 * k + q] = c[q];
+      rr->x[3 * k + q] = x[q];
+    }
+    rr->io[k] = io;
+    rr->alpha[k] = alpha;
+    rr->T[k] = T;
+    rr->w[k] = w;
+    T = T * (1.0 - alpha); /* T_{i+1} = prod_{j<=i} (1 - alpha_j) */
+    if (opt->t_min > 0) {
+      double g = fabs(log(T) - log(opt->t_min));
+      if (g < gap) gap = g;
+      if (T < opt->t_min) {
+        ++k;
+        break;
+      }
+    }
+  }
+  rr->n = k;
+  rr->t_end = T;
+  rr->gap = gap;
+  free(hv.h);
+}
+
+int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
+               const int64_t* idx, int64_t m, const orc_outputs* out) {
+  if (sen->width <= 0 || sen->height <= 0) return 1;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t r = idx ? idx[i] : i;
+    double o[3], d[3], tn, tf, tau;
+    uint8_t valid;
+    one_ray(sen, r, o, d, &tn, &tf, &tau, &valid);
+    double C[3] = {0, 0, 0}, D = 0, O = 0, I = 0, Tend = 1.0, gap = INFINITY;
+    int64_t nv = 0;
+    ray_record rr;
+    memset(&rr, 0, sizeof(rr));
+    if (valid) {
+      composite_ray(s, opt, o, d, tn, tf, &rr);
+      for (int64_t k = 0; k < rr.n; ++k) {
+        for (int q = 0; q < 3; ++q) C[q] += rr.w[k] * rr.c[3 * k + q];
+        D += rr.w[k] * rr.tm[k];
+        O += rr.w[k];
+        I += rr.w[k] * rr.io[k];
+      }
+      Tend = rr.t_end;
+      gap = rr.gap;
+      nv = rr.n;
+      for (int q = 0; q < 3; ++q) C[q] += Tend * opt->background[q];
+    }
+    if (out->rgb)
+      for (int q = 0; q < 3; ++q) out->rgb[3 * i + q] = valid ? C[q] : 0.0;
+    if (out->depth) out->depth[i] = D;
+    if (out->opacity) out->opacity[i] = O;
+    if (out->intensity) out->intensity[i] = I;
+    if (out->t_end) out->t_end[i] = valid ? Tend : 1.0;
+    if (out->term_gap) out->term_gap[i] = gap;
+    if (out->n_visits) out->n_visits[i] = (int32_t)nv;
+    if (out->valid) out->valid[i] = valid;
+    if (out->visits) {
+      for (int64_t k = 0; k < out->visits_cap; ++k)
+        out->visits[i * out->visits_cap + k] = k < nv ? rr.vox[k] : -1;
+    }
+    if (valid) rr_free(&rr);
+  }
+  return 0;
+}
+
+#define ADD(p, v)            \
+  do {                       \
+    double _v = (v);         \
+    _Pragma("omp atomic") *(p) += _v; \
+  } while (0)
+
+/* Adjoint of Eq. 1-6 for L = sum_r g_r . outputs_r.  With q_k = (c_k, t_mid,k,
+ * 1, iota_k) and w_k = T_k alpha_k, tau_k = sigma_k delta_k:
+ *   dL/dtau_k = T_{k+1} (g . q_k) - sum_{j>k} w_j (g . q_j) - T_end (g_rgb . bg)
+ * then the chain rule through Eq. 1/6 (density) and Eq. 2 (colour). */
+int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
+                 const int64_t* idx, int64_t m, const double* g_rgb, const double* g_depth,
+                 const double* g_opacity, const double* g_intensity, double* grad) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t r = idx ? idx[i] : i;
+    double o[3], d[3], tn, tf, tau;
+    uint8_t valid;
+    one_ray(sen, r, o, d, &tn, &tf, &tau, &valid);
+    if (!valid) continue;
+    double gc[3] = {0, 0, 0}, gd = 0, go = 0, gi = 0;
+    if (g_rgb)
+      for (int q = 0; q < 3; ++q) gc[q] = g_rgb[3 * i + q];
+    if (g_depth) gd = g_depth[i];
+    if (g_opacity) go = g_opacity[i];
+    if (g_intensity && opt->want_intensity) gi = g_intensity[i];
+    ray_record rr;
+    memset(&rr, 0, sizeof(rr));
+    composite_ray(s, opt, o, d, tn, tf, &rr);
+    int64_t n = rr.n;
+    double* gq = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* suf = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    for (int64_t k = 0; k < n; ++k)
+      gq[k] = gc[0] * rr.c[3 * k] + gc[1] * rr.c[3 * k + 1] + gc[2] * rr.c[3 * k + 2] +
+              gd * rr.tm[k] + go + gi * rr.io[k];
+    double acc = 0;
+    for (int64_t k = n - 1; k >= 0; --k) {
+      suf[k] = acc; /* sum_{j>k} w_j gq_j */
+      acc += rr.w[k] * gq[k];
+    }
+    double gbg = gc[0] * opt->background[0] + gc[1] * opt->background[1] +
+                 gc[2] * opt->background[2];
+    double gam[4];
+    orc_sh_basis(d, gam);
+    for (int64_t k = 0; k < n; ++k) {
+      int32_t v = rr.vox[k];
+      const double* rec = s->params + (size_t)REC * v;
+      double* gr = grad + (size_t)REC * v;
+      double Tn = rr.T[k] * (1.0 - rr.alpha[k]);
+      double dtau = Tn * gq[k] - suf[k] - rr.t_end * gbg;
+      double dsig = dtau * rr.dl[k];
+      const double* x = rr.x + 3 * k;
+      double xh[4] = {x[0], x[1], x[2], 1.0};
+      if (s->mode == 0) {
+        for (int a = 0; a < 4; ++a) ADD(&gr[a], dsig * rr.sig[k] * xh[a]);
+      } else {
+        double a = rec[25], b = rec[26], sp = rr.lin[k];
+        double ex = exp(-fabs(sp) / b);
+        double ds = dsig * (a / (2.0 * b)) * ex;
+        for (int q = 0; q < 4; ++q) ADD(&gr[q], ds * xh[q]);
+        ADD(&gr[25], dsig * rr.sig[k] / a);
+        ADD(&gr[26], dsig * (-a * sp * ex / (2.0 * b * b)));
+      }
+      for (int q = 0; q < 3; ++q) {
+        double cq = rr.c[3 * k + q];
+        double dz = rr.w[k] * gc[q] * cq * (1.0 - cq);
+        for (int a = 0; a < 3; ++a) ADD(&gr[4 + 3 * q + a], dz * x[a]);
+        for (int b = 0; b < 4; ++b) ADD(&gr[13 + 4 * q + b], dz * gam[b]);
+      }
+      if (opt->want_intensity) {
+        double io = rr.io[k];
+        double dz = rr.w[k] * gi * io * (1.0 - io);
+        for (int a = 0; a < 4; ++a) ADD(&gr[27 + a], dz * xh[a]);
+      }
+    }
+    free(gq);
+    free(suf);
+    rr_free(&rr);
+  }
+  return 0;
+}
