@@ -1,0 +1,478 @@
+#!/usr/bin/env python
+"""Benchmark of the SaLF ray-cast hot path on GB300.
+
+Headline: Mrays/s for a 1920x1080 pinhole camera (60 deg horizontal FOV, one
+ray per pixel) over the seeded 2,000,000-voxel synthetic driving scene (FP32
+records, Eq. 1 density), forward only.  Extra sections on the same JSON line:
+128x2048 spinning LiDAR and 1920x1080 190-degree fisheye on the same scene,
+forward + adjoint for 8 cameras 960x640 on a 1M-voxel BF16 scene, and the
+continuous-batching server on a 4M-voxel BF16 scene (p50 / p99 latency).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl salf|reference]
+N > 1 runs as independent replicas (launched with torch.distributed.run), one
+per GPU: rays are independent, nothing is exchanged.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Mrays/s, 1080p pinhole camera, 2M-voxel driving scene (FP32, forward)"
+WORKLOAD = "pinhole 1920x1080, 60deg hFOV, 1 ray/pixel, driving scene 2,000,000 voxels (seed 2)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = ["paper_2507_18713_gb300/csrc/render.cu", "paper_2507_18713_gb300/csrc/traverse.cuh",
+                  "paper_2507_18713_gb300/csrc/salf_internal.h"]
+FALLBACK_HBM_GBS = 6800.0
+
+# algorithmic bytes (Eq. 1-2 record scalars read per visit, outputs per ray)
+B_FIELD_EXP_F32 = 25 * 4
+B_FIELD_EXP_INT_F32 = 29 * 4
+B_FIELD_EXP_BF16 = 25 * 2
+B_OUT_CAMERA = 20
+B_OUT_LIDAR = 12
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        p = json.load(open(PEAKS_FILE))
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def driving_camera():
+    return synth.pinhole(1920, 1080, 60.0, synth.camera_pose_looking((0.0, 0.0, 1.7), 0.0))
+
+
+def driving_lidar():
+    return synth.lidar(128, 2048, synth.lidar_pose((0.0, 0.0, 1.9), 0.0),
+                       synth.lidar_pose((1.0, 0.0, 1.9), 0.02), t0=0.0, t1=0.1)
+
+
+def driving_fisheye():
+    return synth.fisheye(1920, 1080, 190.0, synth.camera_pose_looking((0.0, 0.0, 1.7), 0.0))
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for(torch, dev: int) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+# --------------------------------------------------------------------- timing
+
+def timed_renders(torch, fn, steps, warmup, flush):
+    """Per-step CUDA-event durations (ms) of fn(), L2 flushed between steps."""
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(st)
+        fn()
+        b.record(st)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def visits_of(torch, gscene, sensor, want_intensity=False):
+    out = gscene.render(sensor, saved=True, outputs=("opacity",), want_intensity=want_intensity)
+    torch.cuda.synchronize()
+    s = out["saved"]
+    return int(s[:, 7].double().sum().item()), out
+
+
+def section(torch, P, gscene, sensor, steps, warmup, flush, b_field, b_out, want_intensity=False,
+            rays_counted=None):
+    R = sensor["width"] * sensor["height"]
+    outputs = ("rgb", "depth", "opacity") if sensor["kind"] != "lidar" else ("depth", "opacity", "intensity")
+    out = {k: torch.empty((R, 3) if k == "rgb" else (R,), device="cuda") for k in outputs}
+    fn = lambda: gscene.render(sensor, outputs=outputs, out=out, valid=False,
+                               want_intensity=want_intensity)
+    ms = timed_renders(torch, fn, steps, warmup, flush)
+    nvis, sv = visits_of(torch, gscene, sensor, want_intensity)
+    n_rays = R if rays_counted is None else rays_counted
+    avg = sum(ms) / len(ms)
+    bytes_alg = nvis * b_field + R * b_out
+    return dict(ms=avg, ms_median=statistics.median(ms), rays=n_rays,
+                mrays_s=n_rays / (avg * 1e-3) / 1e6, fps=1e3 / avg, visits=nvis,
+                visits_per_ray=nvis / R, bytes_alg=bytes_alg,
+                achieved_gbs=bytes_alg / (avg * 1e-3) / 1e9)
+
+
+# --------------------------------------------------------------------- extras
+
+def bench_backward(torch, P, steps, warmup, flush):
+    sc = synth.driving_scene(1_000_000, seed=4, ground_extent=141.4, n_actors=140)
+    g = P.Scene(sc, dtype="bf16")
+    cams = [synth.pinhole(960, 640, 60.0, synth.camera_pose_looking(
+        (5.0 * math.cos(k * math.pi / 4), 5.0 * math.sin(k * math.pi / 4), 1.7), k * math.pi / 4))
+        for k in range(8)]
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    targets = [torch.rand((960 * 640, 3), device="cuda", generator=gen) for _ in cams]
+    dparams = torch.zeros((sc.n, 32), device="cuda")
+    R = 960 * 640
+    outs = [dict(rgb=torch.empty((R, 3), device="cuda"), saved=torch.empty((R, 8), device="cuda"))
+            for _ in cams]
+    inv = 1.0 / (R * 3 * len(cams))
+
+    def step():
+        dparams.zero_()
+        for cam, o, tg in zip(cams, outs, targets):
+            g.render(cam, outputs=("rgb",), saved=True, out=o, valid=False)
+            grad = (o["rgb"] - tg).mul_(2 * inv)
+            g.backward(cam, o["saved"], d_rgb=grad, d_params=dparams)
+
+    ms = timed_renders(torch, step, max(3, steps // 20), warmup, flush)
+    g.check()
+    avg = sum(ms) / len(ms)
+    return dict(workload="8 pinhole 960x640, driving scene 1,000,000 voxels (seed 4), BF16 "
+                "records, FP32 grads, MSE vs U[0,1] targets",
+                ms_per_step=avg, mrays_s=len(cams) * R / (avg * 1e-3) / 1e6)
+
+
+def bench_serving(torch, P, duration_s=5.0, seed=6):
+    sc = synth.driving_scene(4_000_000, seed=3, ground_layers=2, n_actors=600)
+    g = P.Scene(sc, dtype="bf16")
+    rng = np.random.default_rng(seed)
+    kinds = ([("pinhole", 1920, 1080)] * 8 + [("fisheye", 1280, 960)] * 4 + [("pano", 4096, 1024)] * 2
+             + [("lidar", 2048, 128)] * 4 + [("lidar", 1024, 64)] * 2)
+    events = []
+    for si, (k, w, h) in enumerate(kinds):
+        t = rng.exponential(0.1)
+        while t < duration_s:
+            events.append((t, si))
+            t += rng.exponential(0.1)
+    events.sort()
+
+    def make(si):
+        k, w, h = kinds[si]
+        yaw = si * 2 * math.pi / len(kinds) + rng.normal(0, 0.05)
+        pos = (rng.normal(0, 0.5), rng.normal(0, 0.5), 1.7 + rng.normal(0, 0.05))
+        if k == "pinhole":
+            return synth.pinhole(w, h, 60.0, synth.camera_pose_looking(pos, yaw))
+        if k == "fisheye":
+            return synth.fisheye(w, h, 190.0, synth.camera_pose_looking(pos, yaw))
+        if k == "pano":
+            return synth.panorama(w, h, synth.camera_pose_looking(pos, yaw))
+        return synth.lidar(h, w, synth.lidar_pose((pos[0], pos[1], 1.9), yaw),
+                           synth.lidar_pose((pos[0] + 1.0, pos[1], 1.9), yaw + 0.02), t0=0.0, t1=0.1)
+
+    reqs = [(t, make(si)) for t, si in events]
+    total_rays = sum(s["width"] * s["height"] for _, s in reqs)
+    # continuous batching
+    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=2)
+    warm = [srv.submit(s, want_intensity=s["kind"] == "lidar") for _, s in reqs[:8]]
+    for t in warm:
+        srv.poll(t, -1)
+        srv.release(t)
+    srv.close()
+    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=2)
+    t0 = time.perf_counter()
+    tickets = []
+    for at, s in reqs:
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        tickets.append(srv.submit(s, want_intensity=s["kind"] == "lidar"))
+    for t in tickets:
+        srv.poll(t, -1)
+        srv.release(t)
+    t_end = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # sequential plain rendering of the same trace (one render at a time)
+    lat = []
+    t0 = time.perf_counter()
+    for at, s in reqs:
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        g.render(s, want_intensity=s["kind"] == "lidar")
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - t0 - at) * 1e3)
+    t_seq = time.perf_counter() - t0
+    lat.sort()
+    q = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
+    return dict(workload=f"20 sensors at 10 Hz Poisson for {duration_s:.0f} s, driving scene "
+                "4,000,000 voxels (seed 3), BF16 records", requests=len(reqs),
+                offered_mrays_s=total_rays / duration_s / 1e6,
+                batched=dict(p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], launches=st["launches"],
+                             mrays_s=total_rays / t_end / 1e6, wall_s=t_end),
+                sequential=dict(p50_ms=q(0.5), p99_ms=q(0.99), mrays_s=total_rays / t_seq / 1e6,
+                                wall_s=t_seq))
+
+
+# --------------------------------------------------------------------- oracle
+
+def oracle_rate(scene_or, sensor, n_sample, seed):
+    import oracle
+    idx = synth.sample_ray_indices(sensor["width"] * sensor["height"], n_sample, seed)
+    t = time.perf_counter()
+    oracle.render(scene_or, sensor, idx=idx)
+    dt = time.perf_counter() - t
+    return n_sample / dt / 1e6, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores, same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sc = synth.driving_scene(2_000_000, seed=2)
+    osc = oracle.OracleScene(sc)
+    cam = driving_camera()
+    R = cam["width"] * cam["height"]
+    rate, _, cores = oracle_rate(osc, cam, 8192, 100)
+    budget_s = 90.0
+    per_step = int(max(1024, min(R, rate * 1e6 * budget_s / max(1, args.steps + args.warmup))))
+    for w in range(args.warmup):
+        oracle_rate(osc, cam, per_step, 200 + w)
+    times = []
+    for k in range(args.steps):
+        _, dt, _ = oracle_rate(osc, cam, per_step, 300 + k)
+        times.append(dt)
+    tot = sum(times)
+    value = per_step * args.steps / tot / 1e6
+    line = dict(metric=METRIC, value=value, unit="Mrays/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=tot / args.steps * 1e3, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=WORKLOAD, sample=f"{per_step} seeded rays of the frame per step"),
+                cpu_baseline=dict(value=value, unit="Mrays/s", cores=cores, kind="oracle",
+                                  sample=f"{per_step} seeded rays of the 1080p frame per step"),
+                e2e=dict(value=value, unit="Mrays/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="salf", choices=["salf", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="headline only")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_2507_18713_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    P.load()
+    ctx = P.Context(local)
+
+    sc = synth.driving_scene(2_000_000, seed=2)
+    g = P.Scene(sc, dtype="f32", ctx=ctx)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 2x L2
+    cam = driving_camera()
+    R = cam["width"] * cam["height"]
+    out = {k: torch.empty((R, 3) if k == "rgb" else (R,), device="cuda")
+           for k in ("rgb", "depth", "opacity")}
+    fn = lambda: g.render(cam, out=out, valid=False)
+
+    sampler = ClockSampler(gpu_id_for(torch, local))
+    for _ in range(args.warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ms = timed_renders(torch, fn, args.steps, 0, flush)
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    g.check()
+    tot_ms = sum(ms)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    avg = tot_ms / args.steps
+    value = world * R * args.steps / (tot_ms * 1e-3) / 1e6
+
+    nvis, _ = visits_of(torch, g, cam)
+    bytes_alg = nvis * B_FIELD_EXP_F32 + R * B_OUT_CAMERA
+    peak, peak_kind = hbm_peak()
+    achieved = bytes_alg / (avg * 1e-3) / 1e9
+    traffic = None
+    try:
+        tj = json.load(open(TRAFFIC_FILE))
+        if tj.get("kernel_hash") == kernel_hash():
+            traffic = tj.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+
+    # end to end through the C ABI with host output buffers (pinned)
+    host = {k: torch.empty((R, 3) if k == "rgb" else (R,), dtype=torch.float32, pin_memory=True)
+            for k in ("rgb", "depth", "opacity")}
+    for _ in range(args.warmup):
+        g.render_host(cam, out=host)
+    e2e_steps = max(10, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.render_host(cam, out=host)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * R * e2e_steps / e2e_s / 1e6
+
+    line = dict(metric=METRIC, value=value, unit="Mrays/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=avg, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=WORKLOAD, l2="flushed between timed steps (256 MiB write)",
+                            parallelism=f"replicas x{world}", fps=1e3 / avg,
+                            visits_per_ray=nvis / R, t_min=1e-4),
+                roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s",
+                              frac=achieved / peak, traffic=traffic,
+                              peak_source=f"{peak_kind} hbm_gbs",
+                              bytes_per_launch=bytes_alg,
+                              kernel="k_forward<F32,EXP>"),
+                e2e=dict(value=e2e_value, unit="Mrays/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=R * 20,
+                         how="salf_render_rays with pinned host output buffers, synchronous"),
+                gpu_launches=args.steps, clocks=clocks)
+
+    if not args.no_extras and rank == 0:
+        lid = driving_lidar()
+        line["lidar"] = section(torch, P, g, lid, max(50, args.steps // 4), args.warmup, flush,
+                                B_FIELD_EXP_INT_F32, B_OUT_LIDAR, want_intensity=True)
+        line["lidar"]["workload"] = "spinning LiDAR 128x2048, per-ray pose, intensity, same scene"
+        line["lidar"]["roofline_frac"] = line["lidar"]["achieved_gbs"] / peak
+        fe = driving_fisheye()
+        fe_valid = int(g.render(fe, outputs=("opacity",))["valid"].sum().item())
+        line["fisheye"] = section(torch, P, g, fe, max(50, args.steps // 4), args.warmup, flush,
+                                  B_FIELD_EXP_F32, B_OUT_CAMERA, rays_counted=fe_valid)
+        line["fisheye"]["workload"] = "equidistant fisheye 1920x1080 190deg, valid rays counted"
+        line["fisheye"]["roofline_frac"] = line["fisheye"]["achieved_gbs"] / peak
+        del g
+        torch.cuda.empty_cache()
+        line["train_step"] = bench_backward(torch, P, args.steps, args.warmup, flush)
+        torch.cuda.empty_cache()
+        line["serving"] = bench_serving(torch, P, args.serve_seconds)
+
+    if rank == 0:
+        try:
+            import oracle
+            oracle.build()
+            osc = oracle.OracleScene(sc)
+            n_s = 131072
+            rate, dt, cores = oracle_rate(osc, cam, n_s, 99)
+            line["cpu_baseline"] = dict(value=rate, unit="Mrays/s", cores=cores, kind="oracle",
+                                        sample=f"{n_s} seeded rays of the 1080p frame "
+                                        f"({dt:.1f} s wall)")
+        except Exception as e:  # the baseline is reported, never required
+            line["cpu_baseline"] = dict(value=None, unit="Mrays/s", cores=None, kind="oracle",
+                                        sample=f"failed: {e}")
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,291 @@
+/*
+ * salf.h -- C ABI of the GB300 (sm_103a) SaLF ray-cast renderer.
+ *
+ * SaLF (arXiv 2507.18713) represents a scene as a sparse set of disjoint,
+ * axis-aligned cubic voxels on a multi-level grid (Sec. III-A), each holding a
+ * small local field: a density (Eq. 1, or an SDF turned into a density by
+ * Eq. 5-6) and a colour with l <= 1 spherical harmonics (Eq. 2).  A ray is
+ * rendered by visiting the voxels it crosses front to back, sampling each
+ * voxel's field at the midpoint of the ray-voxel segment and compositing by
+ * Eq. 3-4 (Sec. III-A "Volume rendering", Sec. III-B "Ray-Casting with Octree
+ * Acceleration").
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a salf_status; nothing aborts, throws or traps.  On
+ *     failure salf_last_error() gives a thread-local message.
+ *   - Render calls are asynchronous and ordered on the caller's CUDA stream
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream),
+ *     unless the outputs are host memory (salf_outputs.on_host = 1), in which
+ *     case the call also copies the results back and returns after the stream
+ *     has drained.
+ *   - Output buffers are owned by the caller.  Contexts, scenes and servers
+ *     are owned by the library (created/destroyed through this API).
+ *   - World frame: metres, right-handed, z up.  Camera frame: x right, y down,
+ *     z forward.  LiDAR frame: x forward, y left, z up.
+ *   - Ray index of pixel (u, v) (or LiDAR azimuth column u, beam row v) is
+ *     v * width + u.  Per-ray outputs are dense arrays over that index.
+ */
+#ifndef SALF_H
+#define SALF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SALF_OK = 0,
+  SALF_ERR_INVALID = 1,   /* bad argument (null pointer, size, enum, range) */
+  SALF_ERR_OOM = 2,       /* device or host allocation failed */
+  SALF_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  SALF_ERR_OVERLAP = 4,   /* scene voxels overlap (Sec. III-D requires disjoint voxels) */
+  SALF_ERR_AGAIN = 5,     /* serving: request not admitted yet */
+  SALF_ERR_TIMEOUT = 6,   /* serving: wait ran out */
+  SALF_ERR_NOT_FOUND = 7, /* serving: unknown or released ticket */
+  SALF_ERR_SHUTDOWN = 8,  /* serving: server is shutting down */
+  SALF_ERR_DEVICE = 9     /* a kernel reported an internal error through its status word */
+} salf_status;
+
+typedef enum { SALF_FIELD_EXP = 0, SALF_FIELD_SDF = 1 } salf_field_mode;
+typedef enum { SALF_F32 = 0, SALF_BF16 = 1 } salf_dtype;
+typedef enum {
+  SALF_PINHOLE = 0,
+  SALF_FISHEYE_EQUIDIST = 1,
+  SALF_PANO_EQUIRECT = 2,
+  SALF_LIDAR_SPIN = 3,
+  SALF_RAYS_EXPLICIT = 4
+} salf_sensor_kind;
+
+typedef struct salf_ctx salf_ctx;
+typedef struct salf_scene salf_scene;
+typedef struct salf_server salf_server;
+
+/* Number of scalars in one voxel record (Sec. III-A learnable parameters). */
+#define SALF_RECORD_SCALARS 32
+
+/*
+ * Scene input (Sec. III-A).  The root volume is a grid of dims[0..2] cubic
+ * cells of edge s0 with min corner `origin`; a cell of level l has edge
+ * s0 / 2^l and 0 <= level <= max_level (K, at most 10).  Voxel v is the cell
+ * ijk[3v..3v+2] of level level[v].  Voxels must be disjoint (Sec. III-D): a
+ * voxel whose ancestor is also present, or a duplicate, gives SALF_ERR_OVERLAP.
+ * dims[a] << max_level must not exceed 2^21.
+ *
+ * Record layout (32 scalars per voxel, input order):
+ *   [0:4]   W_sigma (Eq. 1) or W_s (Eq. 5): 3 slopes, then the bias
+ *   [4:13]  W_c (Eq. 2), row-major 3x3 (rows r, g, b; columns x, y, z)
+ *   [13:25] W_sh (Eq. 2), row-major 3x4 (rows r, g, b; SH basis
+ *           gamma(w) = [C0, C1 w_y, C1 w_z, C1 w_x], C0 = 1/(2 sqrt(pi)),
+ *           C1 = sqrt(3)/(2 sqrt(pi)), w = unit ray direction)
+ *   [25] a, [26] b (Eq. 6; SDF mode requires a > 0 and b > 0)
+ *   [27:31] W_int: intensity field sigmoid(W_int . [x, 1]), 3 slopes then bias
+ *   [31]    unused
+ * `params` are FP32 (host memory, or device memory if params_on_device);
+ * `dtype` selects how the scene stores them (FP32, or BF16 converted by
+ * round-to-nearest; all arithmetic is FP32 either way).  level and ijk are
+ * host memory.  Everything is copied: the caller may free its arrays when
+ * salf_build_scene returns.
+ */
+typedef struct {
+  int64_t n;
+  double origin[3];
+  double s0;
+  int32_t dims[3];
+  int32_t max_level;
+  const uint8_t* level;
+  const int32_t* ijk;
+  int32_t mode;   /* salf_field_mode */
+  int32_t dtype;  /* salf_dtype */
+  const float* params;
+  int32_t params_on_device;
+} salf_scene_desc;
+
+/*
+ * A sensor (Fig. 2; Sec. V-C rolling shutter).  width x height rays:
+ *   PINHOLE: direction (( u+0.5-cx)/fx, (v+0.5-cy)/fy, 1), normalised.
+ *   FISHEYE_EQUIDIST: theta = |((u+0.5-cx)/fx, (v+0.5-cy)/fy)| is the angle off
+ *     the optical axis (image radius = f * theta); rays with theta > fov/2 are
+ *     invalid (valid = 0, outputs 0).
+ *   PANO_EQUIRECT: longitude 2 pi ((u+0.5)/width - 0.5) (0 = optical axis,
+ *     increasing to the right), latitude from elev_max (top) to elev_min
+ *     (bottom) at the pixel centres.
+ *   LIDAR_SPIN: width azimuth columns (azimuth 2 pi u / width, counter-
+ *     clockwise from sensor +x), height beams with elevations from elev_max
+ *     (row 0) down to elev_min (last row), evenly spaced, inclusive.
+ *   RAYS_EXPLICIT: width rays given as 8 floats (ox, oy, oz, dx, dy, dz,
+ *     t_near, t_far) in `rays` (device memory; host memory only when the
+ *     outputs are on the host); directions are normalised; t_far <= 0 means
+ *     unbounded.
+ * pose0 / pose1: sensor-to-world 3x4 row-major [R | t] at times t0 / t1.  Per-
+ * ray time: LiDAR column u -> t0 + (u/width)(t1 - t0); camera row v ->
+ * t0 + (v/(height-1))(t1 - t0) if rolling_shutter, else t0.  The pose at a
+ * time is the linear interpolation of the translations and the spherical
+ * linear interpolation of the rotations (pose0 exactly at t0).
+ * Rays start at t_near (>= 0) and end at t_far (<= 0: unbounded), in metres
+ * along the unit direction.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float fov;
+  float elev_min, elev_max;
+  double pose0[12], pose1[12];
+  double t0, t1;
+  int32_t rolling_shutter;
+  float t_near, t_far;
+  const float* rays;
+} salf_sensor;
+
+/*
+ * Render options.  t_min_transmittance: a ray stops after compositing the
+ * voxel that brings its transmittance below this value (0 = never stop).
+ * background is added as T_end * background to the (premultiplied) colour.
+ * want_intensity: also evaluate the intensity field.  visits_cap > 0 records,
+ * per ray, the first visits_cap composited voxels (input indices, -1 padded)
+ * and the total count: a debugging aid that slows the kernel.
+ */
+typedef struct {
+  float t_min_transmittance;
+  float background[3];
+  int32_t want_intensity;
+  int32_t visits_cap;
+} salf_render_opts;
+
+/*
+ * Per-ray outputs (R = width * height entries each; NULL = not wanted):
+ *   rgb       R x 3: sum_i T_i alpha_i c_i (Eq. 3) + T_end * background
+ *   depth     R: sum_i T_i alpha_i t_mid,i (expected distance, unnormalised;
+ *             LiDAR range)
+ *   opacity   R: sum_i T_i alpha_i = 1 - T_end
+ *   intensity R: sum_i T_i alpha_i iota_i
+ *   saved     R x 8: (C_r, C_g, C_b, depth, opacity, intensity, T_end,
+ *             visited count as float) -- the input salf_render_backward needs
+ *   valid     R bytes: 1 if the ray exists (fisheye rays outside the FOV: 0)
+ *   visit_count, visits: see salf_render_opts.visits_cap
+ *   ray_dump  R x 8 (debugging aid): the generated ray as (ox, oy, oz, dx, dy,
+ *             dz, time, valid) in world coordinates
+ * on_host = 0: device pointers; on_host = 1: host pointers (the library renders
+ * into its own device staging buffers and copies back before returning).
+ */
+typedef struct {
+  float* rgb;
+  float* depth;
+  float* opacity;
+  float* intensity;
+  float* saved;
+  uint8_t* valid;
+  int32_t* visit_count;
+  int32_t* visits;
+  float* ray_dump;
+  int32_t on_host;
+} salf_outputs;
+
+typedef struct {
+  int64_t n;
+  int32_t mode, dtype;
+  int32_t max_level;
+  int32_t dims[3];
+  int64_t n_level0_cells;   /* occupied level-0 cells */
+  int64_t n_nodes;          /* subdivision nodes below level 0 */
+  int64_t device_bytes;     /* device memory held by the scene */
+  const void* dev_params;   /* records in the scene's internal (Morton) order */
+  const int32_t* dev_order; /* internal index -> input index */
+} salf_scene_info;
+
+/* Create a context bound to CUDA device `device`. */
+salf_status salf_create(int32_t device, salf_ctx** out);
+void salf_destroy(salf_ctx* ctx);
+
+/*
+ * Build a scene (Sec. III-A representation, Sec. III-B acceleration
+ * structure).  Voxels are sorted in Morton order of their min corner, checked
+ * for overlaps, and indexed by an occupancy pyramid of 64-bit masks over 4^3
+ * blocks (with rank offsets into the level-0 cell table) plus 8-way
+ * subdivision nodes below level 0.  Synchronous.  Errors: INVALID (sizes,
+ * ranges, SDF a or b <= 0), OVERLAP, OOM, CUDA.
+ */
+salf_status salf_build_scene(salf_ctx* ctx, const salf_scene_desc* desc, salf_scene** out);
+void salf_scene_destroy(salf_scene* scene);
+salf_status salf_scene_get_info(const salf_scene* scene, salf_scene_info* info);
+
+/*
+ * Replace the scene's records with `params` (n x 32 FP32, input order, host
+ * or device), converting to the scene's storage dtype.  Ordered on `stream`;
+ * host params are copied before the call returns.  The voxel set is unchanged.
+ */
+salf_status salf_scene_update_params(salf_scene* scene, const float* params,
+                                     int32_t params_on_device, void* stream);
+
+/*
+ * Render all rays of `sensor` (Eq. 1-6 along the voxels each ray crosses).
+ * Errors: INVALID (sizes, kind, no output requested), CUDA, DEVICE.
+ */
+salf_status salf_render_rays(salf_scene* scene, const salf_sensor* sensor,
+                             const salf_render_opts* opts, const salf_outputs* out,
+                             void* stream);
+
+/*
+ * Adjoint of salf_render_rays (gradients of Eq. 1-6 compositing, transmittance
+ * recomputed front to back).  `saved` is the R x 8 array the forward call wrote
+ * with the same scene, sensor and options.  d_rgb (R x 3), d_depth,
+ * d_opacity, d_intensity (R each; NULL = zero) are dL/d(outputs).  d_params
+ * (n x 32 FP32, input order, device memory) is ACCUMULATED (+=) with dL/d
+ * (record scalars); scalars a field mode does not use receive no gradient.
+ * All pointers are device memory.  Asynchronous on `stream`.
+ */
+salf_status salf_render_backward(salf_scene* scene, const salf_sensor* sensor,
+                                 const salf_render_opts* opts, const float* saved,
+                                 const float* d_rgb, const float* d_depth,
+                                 const float* d_opacity, const float* d_intensity,
+                                 float* d_params, void* stream);
+
+/* Check the scene's device status word (synchronises the device).  Returns
+ * SALF_ERR_DEVICE if a kernel hit an internal bound since the last check. */
+salf_status salf_scene_check(salf_scene* scene);
+
+/*
+ * Serving: a host scheduler thread batches requests from many sensors over
+ * one resident scene.  mem_budget_bytes bounds the device memory of in-flight
+ * requests (outputs); a request waits until its outputs fit (admission by
+ * memory).  Admitted requests are packed into batched launches on n_streams
+ * streams, so requests that arrive while others run start without waiting
+ * for them to finish.  Each request's outputs are identical to a lone
+ * salf_render_rays call (rays are independent; no cross-ray reductions).
+ */
+typedef struct {
+  int64_t submitted, completed, rejected;
+  int64_t launches;
+  int64_t rays;
+  double p50_ms, p99_ms, max_ms;  /* submit -> completion, completed requests */
+  int64_t peak_bytes;
+} salf_serve_stats;
+
+salf_status salf_serve_create(salf_scene* scene, size_t mem_budget_bytes, int32_t n_streams,
+                              salf_server** out);
+/* Non-blocking.  The sensor descriptor is copied; explicit rays must stay
+ * valid (device memory) until the request completes.  Errors: INVALID (bad
+ * sensor, or outputs larger than the whole budget), SHUTDOWN. */
+salf_status salf_serve_submit(salf_server* srv, const salf_sensor* sensor,
+                              const salf_render_opts* opts, uint64_t* ticket);
+/* Wait up to timeout_ms (0 = just look, < 0 = forever) for `ticket`.  On
+ * completion *done = 1 and `result` receives device pointers into library-
+ * owned memory (rgb, depth, opacity, intensity, valid; saved = NULL), valid
+ * until salf_serve_release.  Returns TIMEOUT if not done in time (with
+ * *done = 0), NOT_FOUND for unknown tickets. */
+salf_status salf_serve_poll(salf_server* srv, uint64_t ticket, int32_t timeout_ms,
+                            salf_outputs* result, int32_t* done);
+salf_status salf_serve_release(salf_server* srv, uint64_t ticket);
+salf_status salf_serve_get_stats(salf_server* srv, salf_serve_stats* stats);
+/* Stops accepting requests, waits for in-flight work, frees everything. */
+void salf_serve_destroy(salf_server* srv);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* salf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

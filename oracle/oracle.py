@@ -48,7 +48,7 @@ class _Sensor(C.Structure):
                 ("fov", C.c_double), ("elev_min", C.c_double), ("elev_max", C.c_double),
                 ("pose0", C.c_double * 12), ("pose1", C.c_double * 12), ("t0", C.c_double),
                 ("t1", C.c_double), ("rolling_shutter", C.c_int32), ("t_near", C.c_double),
-                ("t_far", C.c_double), ("rays", C.c_void_p)]
+                ("t_far", C.c_double), ("rays", C.c_void_p), ("rays64", C.c_void_p)]
 
 
 class _Opts(C.Structure):
@@ -159,8 +159,12 @@ def _sensor(s):
     c.t_near, c.t_far = float(s["t_near"]), float(s["t_far"])
     keep = None
     if s["kind"] == "explicit":
-        keep = np.ascontiguousarray(s["rays"], dtype=np.float32)
-        c.rays = keep.ctypes.data
+        if np.asarray(s["rays"]).dtype == np.float64:
+            keep = np.ascontiguousarray(s["rays"], dtype=np.float64)
+            c.rays64 = keep.ctypes.data
+        else:
+            keep = np.ascontiguousarray(s["rays"], dtype=np.float32)
+            c.rays = keep.ctypes.data
     return c, keep
 
 

@@ -486,7 +486,8 @@ static void one_ray(const orc_sensor* sen, int64_t r, double o[3], double d[3], 
   const int64_t W = sen->width, H = sen->height;
   *valid = 1;
   if (sen->kind == 4) {
-    const float* q = sen->rays + 8 * r;
+    double q[8];
+    for (int k = 0; k < 8; ++k) q[k] = sen->rays64 ? sen->rays64[8 * r + k] : (double)sen->rays[8 * r + k];
     double nn = 0;
     for (int a = 0; a < 3; ++a) {
       o[a] = q[a];
@@ -496,7 +497,7 @@ static void one_ray(const orc_sensor* sen, int64_t r, double o[3], double d[3], 
     nn = sqrt(nn);
     for (int a = 0; a < 3; ++a) d[a] /= nn;
     *tn = q[6];
-    *tf = q[7] > 0 ? (double)q[7] : INFINITY;
+    *tf = q[7] > 0 ? q[7] : INFINITY;
     *tau = 0;
     if (!(nn > 0)) *valid = 0;
     return;

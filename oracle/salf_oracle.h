@@ -53,6 +53,7 @@ typedef struct {
   int32_t rolling_shutter;
   double t_near, t_far;  /* t_far <= 0: unbounded */
   const float* rays;     /* explicit: width rows of (o, d, t_near, t_far) */
+  const double* rays64;  /* explicit, FP64 rows (used instead of `rays` when set) */
 } orc_sensor;
 
 typedef struct {

@@ -1,0 +1,8 @@
+"""GB300 (sm_103a) ray-cast renderer for SaLF sparse local fields (arXiv 2507.18713).
+
+The compute path lives in libsalf.so (hand-written CUDA kernels behind the C
+ABI of include/salf.h); this package is the thin Python binding.
+"""
+
+from ._lib import SalfError, library_path, load  # noqa: F401
+from .api import Context, RenderFn, Scene, Server, device_view, n_rays  # noqa: F401

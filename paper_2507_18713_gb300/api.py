@@ -1,0 +1,338 @@
+"""Python binding of libsalf: the names of include/salf.h, torch tensors for
+device memory and streams.  Marshalling only -- no rendering arithmetic here.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_ctx_cache: dict = {}
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Context:
+    """A libsalf context bound to one CUDA device (salf_create)."""
+
+    def __init__(self, device: int = 0):
+        lib = L.load()
+        torch.cuda.init()
+        h = C.c_void_p()
+        L.check(lib.salf_create(int(device), C.byref(h)), "salf_create")
+        self.device = int(device)
+        self._h = h
+
+    @classmethod
+    def default(cls, device: int = 0) -> "Context":
+        if device not in _ctx_cache:
+            _ctx_cache[device] = cls(device)
+        return _ctx_cache[device]
+
+    def __del__(self):
+        try:
+            if self._h:
+                L.load().salf_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def sensor_struct(sensor: dict, keep: list) -> L.Sensor:
+    """salf_sensor from a descriptor dict (synth.sensors format)."""
+    s = L.Sensor()
+    s.kind = L.KIND[sensor["kind"]]
+    s.width, s.height = int(sensor["width"]), int(sensor["height"])
+    s.fx, s.fy, s.cx, s.cy = (float(sensor[k]) for k in ("fx", "fy", "cx", "cy"))
+    s.fov, s.elev_min, s.elev_max = (float(sensor[k]) for k in ("fov", "elev_min", "elev_max"))
+    s.pose0[:] = [float(v) for v in np.asarray(sensor["pose0"], np.float64).ravel()]
+    s.pose1[:] = [float(v) for v in np.asarray(sensor["pose1"], np.float64).ravel()]
+    s.t0, s.t1 = float(sensor["t0"]), float(sensor["t1"])
+    s.rolling_shutter = int(bool(sensor["rolling_shutter"]))
+    s.t_near, s.t_far = float(sensor["t_near"]), float(sensor["t_far"])
+    if sensor["kind"] == "explicit":
+        rays = sensor["rays"]
+        if isinstance(rays, np.ndarray):
+            rays = torch.from_numpy(np.ascontiguousarray(rays, np.float32)).cuda()
+        rays = rays.contiguous()
+        keep.append(rays)
+        s.rays = rays.data_ptr()
+    return s
+
+
+def opts_struct(t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
+                visits_cap=0) -> L.RenderOpts:
+    o = L.RenderOpts()
+    o.t_min_transmittance = float(t_min)
+    o.background[:] = [float(v) for v in background]
+    o.want_intensity = int(bool(want_intensity))
+    o.visits_cap = int(visits_cap)
+    return o
+
+
+def n_rays(sensor: dict) -> int:
+    return int(sensor["width"]) * int(sensor["height"])
+
+
+class Scene:
+    """A built scene (salf_build_scene).  `scene` is a synth.SceneData (or any
+    object with origin, s0, dims, max_level, level, ijk, params, mode)."""
+
+    def __init__(self, scene, dtype: str = "f32", ctx: Context | None = None, params=None):
+        self.ctx = ctx or Context.default()
+        lib = L.load()
+        level = np.ascontiguousarray(scene.level, dtype=np.uint8)
+        ijk = np.ascontiguousarray(scene.ijk, dtype=np.int32)
+        p = scene.params if params is None else params
+        on_dev = isinstance(p, torch.Tensor) and p.is_cuda
+        if on_dev:
+            p = p.contiguous().float()
+        elif isinstance(p, torch.Tensor):
+            p = np.ascontiguousarray(p.numpy(), dtype=np.float32)
+        else:
+            p = np.ascontiguousarray(p, dtype=np.float32)
+        d = L.SceneDesc()
+        d.n = int(level.shape[0])
+        d.origin[:] = [float(v) for v in scene.origin]
+        d.s0 = float(scene.s0)
+        d.dims[:] = [int(v) for v in scene.dims]
+        d.max_level = int(scene.max_level)
+        d.level, d.ijk = level.ctypes.data, ijk.ctypes.data
+        d.mode = L.MODE[scene.mode]
+        d.dtype = L.DTYPE[dtype]
+        d.params = p.data_ptr() if on_dev else p.ctypes.data
+        d.params_on_device = int(on_dev)
+        h = C.c_void_p()
+        if on_dev:
+            torch.cuda.synchronize()
+        L.check(lib.salf_build_scene(self.ctx._h, C.byref(d), C.byref(h)), "salf_build_scene")
+        self._h = h
+        self.n = d.n
+        self.mode = scene.mode
+        self.dtype = dtype
+
+    def close(self):
+        if getattr(self, "_h", None):
+            torch.cuda.synchronize()
+            L.load().salf_scene_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = L.SceneInfo()
+        L.check(L.load().salf_scene_get_info(self._h, C.byref(i)), "salf_scene_get_info")
+        return {k: getattr(i, k) for k, _ in L.SceneInfo._fields_ if k != "dims"} | \
+            {"dims": tuple(i.dims)}
+
+    def check(self):
+        L.check(L.load().salf_scene_check(self._h), "salf_scene_check")
+
+    def update_params(self, params, stream=None):
+        """salf_scene_update_params: params (n, 32) float32, input order."""
+        lib = L.load()
+        if isinstance(params, torch.Tensor) and params.is_cuda:
+            params = params.detach().contiguous().float()
+            L.check(lib.salf_scene_update_params(self._h, params.data_ptr(), 1,
+                                                 _stream_ptr(stream)), "salf_scene_update_params")
+        else:
+            arr = np.ascontiguousarray(params, dtype=np.float32)
+            L.check(lib.salf_scene_update_params(self._h, arr.ctypes.data, 0,
+                                                 _stream_ptr(stream)), "salf_scene_update_params")
+
+    def render(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
+               visits_cap=0, outputs=("rgb", "depth", "opacity"), saved=False, valid=True,
+               stream=None, out: dict | None = None, ray_dump: bool = False) -> dict:
+        """salf_render_rays into (new or given) CUDA tensors; asynchronous on
+        `stream` (default: torch's current stream)."""
+        R = n_rays(sensor)
+        dev = torch.device("cuda", self.ctx.device)
+        res = {} if out is None else dict(out)
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,)}
+        for k in outputs:
+            if k not in res:
+                res[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
+        if saved and "saved" not in res:
+            res["saved"] = torch.empty((R, 8), dtype=torch.float32, device=dev)
+        if valid and "valid" not in res:
+            res["valid"] = torch.empty((R,), dtype=torch.uint8, device=dev)
+        if visits_cap > 0:
+            res.setdefault("visit_count", torch.empty((R,), dtype=torch.int32, device=dev))
+            res.setdefault("visits", torch.empty((R, visits_cap), dtype=torch.int32, device=dev))
+        o = L.Outputs()
+        if ray_dump and "ray_dump" not in res:
+            res["ray_dump"] = torch.empty((R, 8), dtype=torch.float32, device=dev)
+        for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits",
+                  "ray_dump"):
+            if k in res:
+                setattr(o, k, res[k].data_ptr())
+        keep: list = []
+        s = sensor_struct(sensor, keep)
+        op = opts_struct(t_min, background, want_intensity, visits_cap)
+        L.check(L.load().salf_render_rays(self._h, C.byref(s), C.byref(op), C.byref(o),
+                                          _stream_ptr(stream)), "salf_render_rays")
+        if keep:
+            res["_keep"] = keep
+        return res
+
+    def render_host(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                    want_intensity=False, outputs=("rgb", "depth", "opacity"), out=None,
+                    stream=None) -> dict:
+        """salf_render_rays with host output buffers (on_host = 1): synchronous,
+        results land in (pinned, if given) host memory."""
+        R = n_rays(sensor)
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,)}
+        res = out if out is not None else {k: torch.empty(shapes[k], dtype=torch.float32)
+                                           for k in outputs}
+        o = L.Outputs()
+        for k, v in res.items():
+            setattr(o, k, v.data_ptr())
+        o.on_host = 1
+        keep: list = []
+        s = sensor_struct(sensor, keep)
+        op = opts_struct(t_min, background, want_intensity, 0)
+        L.check(L.load().salf_render_rays(self._h, C.byref(s), C.byref(op), C.byref(o),
+                                          _stream_ptr(stream)), "salf_render_rays(host)")
+        return res
+
+    def backward(self, sensor: dict, saved, d_rgb=None, d_depth=None, d_opacity=None,
+                 d_intensity=None, d_params=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                 want_intensity=False, stream=None):
+        """salf_render_backward: returns d_params (n, 32) float32 (accumulated
+        into the given tensor if any)."""
+        dev = torch.device("cuda", self.ctx.device)
+        if d_params is None:
+            d_params = torch.zeros((self.n, 32), dtype=torch.float32, device=dev)
+
+        def ptr(t):
+            return None if t is None else t.contiguous().data_ptr()
+
+        keep = [t.contiguous() for t in (d_rgb, d_depth, d_opacity, d_intensity) if t is not None]
+        s = sensor_struct(sensor, keep)
+        op = opts_struct(t_min, background, want_intensity, 0)
+        L.check(L.load().salf_render_backward(
+            self._h, C.byref(s), C.byref(op), saved.data_ptr(), ptr(d_rgb), ptr(d_depth),
+            ptr(d_opacity), ptr(d_intensity), d_params.data_ptr(), _stream_ptr(stream)),
+            "salf_render_backward")
+        return d_params
+
+
+class RenderFn(torch.autograd.Function):
+    """Differentiable render: (params) -> (rgb, depth, opacity).
+
+    forward uploads `params` (n x 32 FP32, input order) into the scene (in
+    the scene's storage dtype) and renders with saved per-ray totals; backward
+    runs the hand-written adjoint kernel and returns dL/dparams."""
+
+    @staticmethod
+    def forward(ctx, params, scene: Scene, sensor: dict, t_min: float = 1e-4,
+                background=(0.0, 0.0, 0.0)):
+        scene.update_params(params)
+        out = scene.render(sensor, t_min=t_min, background=background, saved=True,
+                           outputs=("rgb", "depth", "opacity"))
+        ctx.scene, ctx.sensor, ctx.t_min, ctx.background = scene, sensor, t_min, background
+        ctx.save_for_backward(out["saved"])
+        return out["rgb"], out["depth"], out["opacity"]
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_opacity):
+        (saved,) = ctx.saved_tensors
+        d = ctx.scene.backward(ctx.sensor, saved, d_rgb=g_rgb, d_depth=g_depth,
+                               d_opacity=g_opacity, t_min=ctx.t_min, background=ctx.background)
+        return d, None, None, None, None
+
+
+class Server:
+    """Continuous-batching render server (salf_serve_*)."""
+
+    def __init__(self, scene: Scene, mem_budget_bytes: int, n_streams: int = 2):
+        h = C.c_void_p()
+        L.check(L.load().salf_serve_create(scene._h, int(mem_budget_bytes), int(n_streams),
+                                           C.byref(h)), "salf_serve_create")
+        self._h = h
+        self.scene = scene
+        self._sensors: dict = {}
+
+    def submit(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
+               want_intensity=False) -> int:
+        keep: list = []
+        s = sensor_struct(sensor, keep)
+        op = opts_struct(t_min, background, want_intensity, 0)
+        t = C.c_uint64()
+        L.check(L.load().salf_serve_submit(self._h, C.byref(s), C.byref(op), C.byref(t)),
+                "salf_serve_submit")
+        self._sensors[t.value] = (sensor, keep)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """Returns None if not done within timeout_ms, else a dict of raw
+        device pointers {rgb, depth, opacity, intensity, valid} (library-owned)."""
+        o = L.Outputs()
+        done = L.c_int32()
+        st = L.load().salf_serve_poll(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(o),
+                                      C.byref(done))
+        if st == L.ERR_TIMEOUT:
+            return None
+        L.check(st, "salf_serve_poll")
+        return {k: getattr(o, k) for k in ("rgb", "depth", "opacity", "intensity", "valid")}
+
+    def fetch(self, ticket: int, timeout_ms: int = -1, copy: bool = True) -> dict | None:
+        """poll + tensors over the results (copies unless copy=False, in which
+        case the views are valid until release)."""
+        ptrs = self.poll(ticket, timeout_ms)
+        if ptrs is None:
+            return None
+        sensor = self._sensors[ticket][0]
+        R = n_rays(sensor)
+        res = {}
+        for k, shape, ts in (("rgb", (R, 3), "<f4"), ("depth", (R,), "<f4"),
+                             ("opacity", (R,), "<f4"), ("intensity", (R,), "<f4"),
+                             ("valid", (R,), "|u1")):
+            if ptrs[k]:
+                t = device_view(ptrs[k], shape, ts)
+                res[k] = t.clone() if copy else t
+        return res
+
+    def release(self, ticket: int):
+        L.check(L.load().salf_serve_release(self._h, C.c_uint64(ticket)), "salf_serve_release")
+        self._sensors.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = L.ServeStats()
+        L.check(L.load().salf_serve_get_stats(self._h, C.byref(s)), "salf_serve_get_stats")
+        return {k: getattr(s, k) for k, _ in L.ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.load().salf_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DevBuf:
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 2,
+                                         "strides": None}
+
+
+def device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
+    """Zero-copy torch view of library-owned device memory."""
+    return torch.as_tensor(_DevBuf(ptr, shape, typestr), device="cuda")

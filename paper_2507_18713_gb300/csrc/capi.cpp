@@ -1,0 +1,430 @@
+// capi.cpp -- C-ABI entry points of libsalf (declared in include/salf.h):
+// context, scene lifetime, request preparation (done in FP64 on the host),
+// render / adjoint dispatch, host-memory staging.
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+
+#include "salf_internal.h"
+
+namespace {
+thread_local std::string g_err;
+}
+
+void salf_set_error(const std::string& msg) { g_err = msg; }
+
+salf_status salf_cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? SALF_ERR_OOM : SALF_ERR_CUDA;
+}
+
+extern "C" const char* salf_last_error(void) { return g_err.c_str(); }
+
+extern "C" salf_status salf_create(int32_t device, salf_ctx** out) {
+  if (!out) {
+    g_err = "salf_create: null out";
+    return SALF_ERR_INVALID;
+  }
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return salf_cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) {
+    g_err = "salf_create: no such device";
+    return SALF_ERR_INVALID;
+  }
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  salf_ctx* c = new salf_ctx();
+  c->device = device;
+  *out = c;
+  return SALF_OK;
+}
+
+extern "C" void salf_destroy(salf_ctx* ctx) { delete ctx; }
+
+extern "C" salf_status salf_build_scene(salf_ctx* ctx, const salf_scene_desc* desc,
+                                        salf_scene** out) {
+  return salf_build_scene_impl(ctx, desc, out);
+}
+
+extern "C" void salf_scene_destroy(salf_scene* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  for (void* p : s->allocations) cudaFree(p);
+  if (s->staging) cudaFree(s->staging);
+  delete s;
+}
+
+extern "C" salf_status salf_scene_get_info(const salf_scene* s, salf_scene_info* info) {
+  if (!s || !info) {
+    g_err = "salf_scene_get_info: null argument";
+    return SALF_ERR_INVALID;
+  }
+  std::memset(info, 0, sizeof(*info));
+  info->n = s->n;
+  info->mode = s->mode;
+  info->dtype = s->dtype;
+  info->max_level = s->K;
+  for (int a = 0; a < 3; ++a) info->dims[a] = s->dims[a];
+  info->n_level0_cells = s->n_cells0;
+  info->n_nodes = s->n_nodes;
+  info->device_bytes = s->device_bytes;
+  info->dev_params = s->dev.params;
+  info->dev_order = s->dev.order;
+  return SALF_OK;
+}
+
+extern "C" salf_status salf_scene_check(salf_scene* s) {
+  if (!s) {
+    g_err = "salf_scene_check: null scene";
+    return SALF_ERR_INVALID;
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(s->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return salf_cuda_fail(e, "kernel");
+  int flag = 0;
+  if ((e = cudaMemcpy(&flag, s->dev.status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return salf_cuda_fail(e, "cudaMemcpy(status)");
+  if (flag) {
+    cudaMemset(s->dev.status, 0, sizeof(int));
+    g_err = "device status word " + std::to_string(flag) +
+            ((flag & SALF_DEVERR_STEP_CAP) ? " (traversal step bound reached)" : "") +
+            ((flag & SALF_DEVERR_SDF_AB) ? " (SDF record with a <= 0 or b <= 0)" : "");
+    return SALF_ERR_DEVICE;
+  }
+  return SALF_OK;
+}
+
+// Grow the scene's staging buffer (caller holds staging_mu).
+static salf_status ensure_staging(salf_scene* s, size_t bytes) {
+  if (s->staging_bytes >= bytes) return SALF_OK;
+  if (s->staging) {
+    cudaDeviceSynchronize();
+    cudaFree(s->staging);
+    s->staging = nullptr;
+    s->staging_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&s->staging, bytes);
+  if (e != cudaSuccess) {
+    s->staging = nullptr;
+    return salf_cuda_fail(e, "cudaMalloc(staging)");
+  }
+  s->staging_bytes = bytes;
+  return SALF_OK;
+}
+
+extern "C" salf_status salf_scene_update_params(salf_scene* s, const float* params,
+                                                int32_t on_device, void* stream) {
+  if (!s || (!params && s->n > 0)) {
+    g_err = "salf_scene_update_params: null argument";
+    return SALF_ERR_INVALID;
+  }
+  if (s->n == 0) return SALF_OK;
+  if (reinterpret_cast<uintptr_t>(params) & 15u) {
+    g_err = "salf_scene_update_params: params must be 16-byte aligned";
+    return SALF_ERR_INVALID;
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(s->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (on_device) {
+    e = salf_launch_gather_params(params, s->dev.order, const_cast<void*>(s->dev.params), s->n,
+                                  s->dtype, s->mode, s->dev.status, st);
+    if (e != cudaSuccess) return salf_cuda_fail(e, "gather params");
+    return SALF_OK;
+  }
+  std::lock_guard<std::mutex> lk(s->staging_mu);
+  const size_t bytes = (size_t)s->n * 128;
+  salf_status rs = ensure_staging(s, bytes);
+  if (rs != SALF_OK) return rs;
+  if ((e = cudaMemcpyAsync(s->staging, params, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return salf_cuda_fail(e, "cudaMemcpyAsync(params)");
+  e = salf_launch_gather_params(static_cast<const float*>(s->staging), s->dev.order,
+                                const_cast<void*>(s->dev.params), s->n, s->dtype, s->mode,
+                                s->dev.status, st);
+  if (e != cudaSuccess) return salf_cuda_fail(e, "gather params");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return salf_cuda_fail(e, "sync");
+  return SALF_OK;
+}
+
+// ------------------------------------------------------------ requests
+
+static void mat_to_quat(const double* P, double q[4]) {
+  // rotation block of a row-major 3x4 [R|t] -> (w, x, y, z), Shoemake's
+  // branch on the largest diagonal term
+  const double r00 = P[0], r01 = P[1], r02 = P[2], r10 = P[4], r11 = P[5], r12 = P[6],
+               r20 = P[8], r21 = P[9], r22 = P[10];
+  const double tr = r00 + r11 + r22;
+  if (tr > 0) {
+    const double s = 2.0 * std::sqrt(tr + 1.0);
+    q[0] = 0.25 * s;
+    q[1] = (r21 - r12) / s;
+    q[2] = (r02 - r20) / s;
+    q[3] = (r10 - r01) / s;
+  } else if (r00 > r11 && r00 > r22) {
+    const double s = 2.0 * std::sqrt(1.0 + r00 - r11 - r22);
+    q[0] = (r21 - r12) / s;
+    q[1] = 0.25 * s;
+    q[2] = (r01 + r10) / s;
+    q[3] = (r02 + r20) / s;
+  } else if (r11 > r22) {
+    const double s = 2.0 * std::sqrt(1.0 + r11 - r00 - r22);
+    q[0] = (r02 - r20) / s;
+    q[1] = (r01 + r10) / s;
+    q[2] = 0.25 * s;
+    q[3] = (r12 + r21) / s;
+  } else {
+    const double s = 2.0 * std::sqrt(1.0 + r22 - r00 - r11);
+    q[0] = (r10 - r01) / s;
+    q[1] = (r02 + r20) / s;
+    q[2] = (r12 + r21) / s;
+    q[3] = 0.25 * s;
+  }
+  const double nn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int k = 0; k < 4; ++k) q[k] /= nn;
+}
+
+int64_t salf_request_rays(const salf_sensor* sen) {
+  return (int64_t)sen->width * (int64_t)sen->height;
+}
+
+salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* s,
+                                 const salf_render_opts* o, ReqDev* r) {
+  std::memset(r, 0, sizeof(*r));
+  if (s->kind < SALF_PINHOLE || s->kind > SALF_RAYS_EXPLICIT || s->width <= 0 || s->height <= 0 ||
+      (int64_t)s->width * s->height > (int64_t)0x7fffffff) {
+    g_err = "sensor: bad kind or size";
+    return SALF_ERR_INVALID;
+  }
+  if ((s->kind == SALF_PINHOLE || s->kind == SALF_FISHEYE_EQUIDIST) &&
+      !(s->fx > 0 && s->fy > 0 && std::isfinite(s->cx) && std::isfinite(s->cy))) {
+    g_err = "sensor: focal lengths must be > 0";
+    return SALF_ERR_INVALID;
+  }
+  if (s->kind == SALF_RAYS_EXPLICIT && (!s->rays || (reinterpret_cast<uintptr_t>(s->rays) & 15u))) {
+    g_err = "sensor: explicit rays need a 16-byte aligned array";
+    return SALF_ERR_INVALID;
+  }
+  if (!(s->t_near >= 0) || !(o->t_min_transmittance >= 0) || o->visits_cap < 0) {
+    g_err = "sensor/options: t_near and t_min must be >= 0";
+    return SALF_ERR_INVALID;
+  }
+  r->kind = s->kind;
+  r->W = s->width;
+  r->H = s->height;
+  r->inv_fx = s->fx > 0 ? (float)(1.0 / (double)s->fx) : 0.f;
+  r->inv_fy = s->fy > 0 ? (float)(1.0 / (double)s->fy) : 0.f;
+  r->cx = s->cx;
+  r->cy = s->cy;
+  r->half_fov = 0.5f * s->fov;
+  r->elev_min = s->elev_min;
+  r->elev_max = s->elev_max;
+  r->elev_step = s->height > 1 ? (float)(((double)s->elev_max - (double)s->elev_min) / (s->height - 1)) : 0.f;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) r->R0[3 * i + j] = (float)s->pose0[4 * i + j];
+  double q0[4], q1[4];
+  mat_to_quat(s->pose0, q0);
+  mat_to_quat(s->pose1, q1);
+  double dot = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2] + q0[3] * q1[3];
+  if (dot < 0) {
+    dot = -dot;
+    for (int k = 0; k < 4; ++k) q1[k] = -q1[k];
+  }
+  const double th = std::acos(std::min(1.0, dot));
+  r->theta = (float)th;
+  r->inv_sin_theta = th > 1e-4 ? (float)(1.0 / std::sin(th)) : 0.f;
+  for (int k = 0; k < 4; ++k) {
+    r->q0[k] = (float)q0[k];
+    r->q1[k] = (float)q1[k];
+  }
+  const bool timed = s->t1 > s->t0;
+  r->moving = (s->kind == SALF_LIDAR_SPIN && timed) ||
+              ((s->kind <= SALF_PANO_EQUIRECT) && s->rolling_shutter && timed && s->height > 1);
+  const double inv_sfin = 1.0 / sc->sfin;
+  for (int a = 0; a < 3; ++a) {
+    const double g0 = (s->pose0[4 * a + 3] - sc->origin[a]) * inv_sfin;
+    const double g1 = (s->pose1[4 * a + 3] - sc->origin[a]) * inv_sfin;
+    const double f = std::floor(g0);
+    if (!std::isfinite(g0) || !std::isfinite(g1) || std::fabs(g0) > 8.0e6 || std::fabs(g1) > 8.0e6) {
+      g_err = "sensor: pose translation too far from the scene grid";
+      return SALF_ERR_INVALID;
+    }
+    r->Oi[a] = (int)f;
+    r->Of[a] = (float)(g0 - f);
+    r->dO[a] = (float)(g1 - g0);
+  }
+  r->t_near = s->t_near;
+  r->t_far = s->t_far > 0 ? s->t_far : std::numeric_limits<float>::infinity();
+  r->time0 = (float)s->t0;
+  r->time1 = (float)s->t1;
+  r->rays = s->rays;
+  r->t_min = o->t_min_transmittance;
+  for (int k = 0; k < 3; ++k) r->bg[k] = o->background[k];
+  r->want_int = o->want_intensity ? 1 : 0;
+  r->vcap = o->visits_cap;
+  if (s->kind == SALF_RAYS_EXPLICIT || s->height == 1) {
+    r->tile_w = 32;
+    r->tile_h = 1;
+  } else {
+    r->tile_w = SALF_TILE_W;
+    r->tile_h = SALF_TILE_H;
+  }
+  r->tiles_x = (s->width + r->tile_w - 1) / r->tile_w;
+  r->n_tiles = r->tiles_x * ((s->height + r->tile_h - 1) / r->tile_h);
+  return SALF_OK;
+}
+
+static salf_render_opts default_opts() {
+  salf_render_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.t_min_transmittance = 1e-4f;
+  return o;
+}
+
+static bool misaligned(const void* p, unsigned a) {
+  return p && (reinterpret_cast<uintptr_t>(p) & (a - 1));
+}
+
+extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
+                                        const salf_render_opts* opts, const salf_outputs* out,
+                                        void* stream) {
+  if (!sc || !sen || !out) {
+    g_err = "salf_render_rays: null argument";
+    return SALF_ERR_INVALID;
+  }
+  const salf_render_opts o = opts ? *opts : default_opts();
+  if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
+      !(o.visits_cap > 0 && out->visits) && !out->ray_dump) {
+    g_err = "salf_render_rays: no output requested";
+    return SALF_ERR_INVALID;
+  }
+  if (o.visits_cap > 0 && (!out->visits || !out->visit_count)) {
+    g_err = "salf_render_rays: visits_cap > 0 needs visits and visit_count";
+    return SALF_ERR_INVALID;
+  }
+  if (out->on_host && out->ray_dump) {
+    g_err = "salf_render_rays: ray_dump needs device outputs";
+    return SALF_ERR_INVALID;
+  }
+  if (!out->on_host && misaligned(out->saved, 16)) {
+    g_err = "salf_render_rays: saved must be 16-byte aligned";
+    return SALF_ERR_INVALID;
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  LaunchParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.S = sc->dev;
+  P.n_req = 1;
+  ReqDev& r = P.req[0];
+  salf_status st = salf_prepare_request(sc, sen, &o, &r);
+  if (st != SALF_OK) return st;
+  P.total_tiles = r.n_tiles;
+  const size_t R = (size_t)salf_request_rays(sen);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+
+  if (!out->on_host) {
+    r.rgb = out->rgb;
+    r.depth = out->depth;
+    r.opacity = out->opacity;
+    r.intensity = out->intensity;
+    r.saved = out->saved;
+    r.valid = out->valid;
+    r.vcount = out->visit_count;
+    r.visits = out->visits;
+    r.ray_dump = out->ray_dump;
+    if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
+    return SALF_OK;
+  }
+
+  // Host outputs: render into staging, copy back, wait.
+  std::lock_guard<std::mutex> lk(sc->staging_mu);
+  const size_t vcap = (size_t)std::max(0, o.visits_cap);
+  const size_t rays_bytes = sen->kind == SALF_RAYS_EXPLICIT ? R * 32 : 0;
+  size_t off[9], total = 0;
+  const size_t sizes[9] = {out->rgb ? R * 12 : 0, out->depth ? R * 4 : 0, out->opacity ? R * 4 : 0,
+                           out->intensity ? R * 4 : 0, out->saved ? R * 32 : 0,
+                           out->valid ? R : 0, vcap ? R * 4 : 0, vcap ? R * vcap * 4 : 0,
+                           rays_bytes};
+  for (int i = 0; i < 9; ++i) {
+    off[i] = total;
+    total += (sizes[i] + 255) & ~(size_t)255;
+  }
+  if ((st = ensure_staging(sc, total)) != SALF_OK) return st;
+  char* base = static_cast<char*>(sc->staging);
+  r.rgb = out->rgb ? reinterpret_cast<float*>(base + off[0]) : nullptr;
+  r.depth = out->depth ? reinterpret_cast<float*>(base + off[1]) : nullptr;
+  r.opacity = out->opacity ? reinterpret_cast<float*>(base + off[2]) : nullptr;
+  r.intensity = out->intensity ? reinterpret_cast<float*>(base + off[3]) : nullptr;
+  r.saved = out->saved ? reinterpret_cast<float*>(base + off[4]) : nullptr;
+  r.valid = out->valid ? reinterpret_cast<unsigned char*>(base + off[5]) : nullptr;
+  r.vcount = vcap ? reinterpret_cast<int*>(base + off[6]) : nullptr;
+  r.visits = vcap ? reinterpret_cast<int*>(base + off[7]) : nullptr;
+  if (rays_bytes) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, sen->rays) == cudaSuccess && at.type == cudaMemoryTypeDevice) {
+      r.rays = sen->rays;
+    } else {
+      cudaGetLastError();
+      if ((e = cudaMemcpyAsync(base + off[8], sen->rays, rays_bytes, cudaMemcpyHostToDevice, cs)) !=
+          cudaSuccess)
+        return salf_cuda_fail(e, "cudaMemcpyAsync(rays)");
+      r.rays = reinterpret_cast<const float*>(base + off[8]);
+    }
+  }
+  if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
+  struct Cp {
+    void* dst;
+    const void* src;
+    size_t n;
+  } cps[8] = {{out->rgb, r.rgb, sizes[0]},        {out->depth, r.depth, sizes[1]},
+              {out->opacity, r.opacity, sizes[2]}, {out->intensity, r.intensity, sizes[3]},
+              {out->saved, r.saved, sizes[4]},     {out->valid, r.valid, sizes[5]},
+              {out->visit_count, r.vcount, sizes[6]}, {out->visits, r.visits, sizes[7]}};
+  for (const Cp& c : cps) {
+    if (!c.n || !c.dst) continue;
+    if ((e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+      return salf_cuda_fail(e, "cudaMemcpyAsync(outputs)");
+  }
+  if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return salf_cuda_fail(e, "render");
+  return SALF_OK;
+}
+
+extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* sen,
+                                            const salf_render_opts* opts, const float* saved,
+                                            const float* d_rgb, const float* d_depth,
+                                            const float* d_opacity, const float* d_intensity,
+                                            float* d_params, void* stream) {
+  if (!sc || !sen || !saved || !d_params) {
+    g_err = "salf_render_backward: null argument";
+    return SALF_ERR_INVALID;
+  }
+  if (misaligned(saved, 16) || misaligned(d_params, 16)) {
+    g_err = "salf_render_backward: saved and d_params must be 16-byte aligned";
+    return SALF_ERR_INVALID;
+  }
+  const salf_render_opts o = opts ? *opts : default_opts();
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  LaunchParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.S = sc->dev;
+  P.n_req = 1;
+  ReqDev& r = P.req[0];
+  salf_status st = salf_prepare_request(sc, sen, &o, &r);
+  if (st != SALF_OK) return st;
+  r.vcap = 0;
+  r.bsaved = saved;
+  r.g_rgb = d_rgb;
+  r.g_depth = d_depth;
+  r.g_opacity = d_opacity;
+  r.g_int = d_intensity;
+  r.d_params = d_params;
+  P.total_tiles = r.n_tiles;
+  if ((e = salf_launch_backward(P, static_cast<cudaStream_t>(stream))) != cudaSuccess)
+    return salf_cuda_fail(e, "backward launch");
+  return SALF_OK;
+}

@@ -1,0 +1,124 @@
+// render.cu -- fused forward ray-cast kernel (sm_103a).
+//
+// One thread per ray, one warp per 8x4 pixel tile (32 consecutive rays for
+// explicit rays), one launch for a whole batch of requests.  Per ray: sensor
+// ray generation -> traversal of the sparse voxel structure -> Eq. 1/5-6
+// density and Eq. 2 colour at each segment midpoint -> Eq. 3-4 front-to-back
+// compositing, stopping once the transmittance drops below t_min.
+//
+// The loop is "while-while": every live lane first walks (empty leaves are
+// skipped whole) to its next hit voxel, then the lanes that have one gather
+// their records and composite together; the warp leaves the loop when no lane
+// has a hit (ballot).  Lanes whose ray terminated early idle in the ballot.
+#include "traverse.cuh"
+
+using namespace salf;
+
+template <int DT, int MODE, bool DUMP>
+__global__ void __launch_bounds__(256) k_forward(const __grid_constant__ LaunchParams P) {
+  const int warp = blockIdx.x * SALF_WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (warp >= P.total_tiles) return;
+  const int lane = threadIdx.x & 31;
+  const ReqDev& Q = P.req[find_request(P, warp)];
+  const DevScene& S = P.S;
+  const int tile = warp - Q.tile_begin;
+  const int tx = tile % Q.tiles_x, ty = tile / Q.tiles_x;
+  const int u = tx * Q.tile_w + lane % Q.tile_w;
+  const int v = ty * Q.tile_h + lane / Q.tile_w;
+  const bool in_img = (u < Q.W) && (v < Q.H);
+  const int ray = v * Q.W + u;
+
+  Ray r;
+  Walk w;
+  w.alive = false;
+  r.valid = false;
+  r.d[0] = r.d[1] = r.d[2] = 0.f;
+  if (in_img) {
+    gen_ray(Q, S, u, v, ray, r);
+    walk_init(S, r, w);
+    if (DUMP && Q.ray_dump) dump_ray(Q, S, r, ray);
+  }
+  float gam[4];
+  sh_basis(r.d, gam);
+  const bool want_int = Q.want_int != 0;
+  const float tmin = Q.t_min;
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dp = 0.f, Op = 0.f, Ip = 0.f;
+  int nvis = 0;
+
+  for (;;) {
+    Hit h;
+    const bool hit = next_hit(S, w, h);
+    if (!__any_sync(0xffffffffu, hit)) break;
+    if (hit) {
+      Record<DT> rec;
+      rec.load(S.params, h.vox, want_int);
+      const float tm = 0.5f * (h.tin + h.tout);
+      const float dl = h.tout - h.tin;
+      float x[3];
+      local_coords(w, h, tm, x);
+      float lin;
+      const float sig = density<MODE>(rec.v, x, &lin);
+      float c[3];
+      colour(rec.v, x, gam, c);
+      const float io = want_int ? intensity_field(rec.v, x) : 0.f;
+      const float e = __expf(-sig * dl);   // 1 - alpha (Eq. 4)
+      const float wgt = T * (1.f - e);     // T_i alpha_i (Eq. 3)
+      C0 = fmaf(wgt, c[0], C0);
+      C1 = fmaf(wgt, c[1], C1);
+      C2 = fmaf(wgt, c[2], C2);
+      Dp = fmaf(wgt, tm, Dp);
+      Op += wgt;
+      Ip = fmaf(wgt, io, Ip);
+      T *= e;
+      if (DUMP) {
+        if (nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + nvis] = __ldg(&S.order[h.vox]);
+      }
+      ++nvis;
+      if (T < tmin) w.alive = false;
+    }
+  }
+  if (!in_img) return;
+  const bool valid = r.valid;
+  if (Q.rgb) {
+    float* o = Q.rgb + 3 * (size_t)ray;
+    o[0] = valid ? fmaf(T, Q.bg[0], C0) : 0.f;
+    o[1] = valid ? fmaf(T, Q.bg[1], C1) : 0.f;
+    o[2] = valid ? fmaf(T, Q.bg[2], C2) : 0.f;
+  }
+  if (Q.depth) Q.depth[ray] = Dp;
+  if (Q.opacity) Q.opacity[ray] = Op;
+  if (Q.intensity) Q.intensity[ray] = Ip;
+  if (Q.saved) {
+    float4* s = reinterpret_cast<float4*>(Q.saved) + 2 * (size_t)ray;
+    s[0] = make_float4(C0, C1, C2, Dp);
+    s[1] = make_float4(Op, Ip, T, (float)nvis);
+  }
+  if (Q.valid) Q.valid[ray] = valid ? 1 : 0;
+  if (DUMP) {
+    if (Q.vcap > 0) {
+      Q.vcount[ray] = nvis;
+      for (int k = nvis; k < Q.vcap; ++k) Q.visits[(size_t)ray * Q.vcap + k] = -1;
+    }
+  }
+}
+
+template <int DT, int MODE>
+static cudaError_t launch_fm(const LaunchParams& P, bool dump, cudaStream_t st) {
+  const int blocks = (P.total_tiles + SALF_WARPS_PER_BLOCK - 1) / SALF_WARPS_PER_BLOCK;
+  if (blocks == 0) return cudaSuccess;
+  if (dump)
+    k_forward<DT, MODE, true><<<blocks, 32 * SALF_WARPS_PER_BLOCK, 0, st>>>(P);
+  else
+    k_forward<DT, MODE, false><<<blocks, 32 * SALF_WARPS_PER_BLOCK, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
+  bool dump = false;
+  for (int i = 0; i < P.n_req; ++i) dump = dump || P.req[i].vcap > 0 || P.req[i].ray_dump;
+  const int dt = P.S.dtype, md = P.S.mode;
+  if (dt == SALF_F32 && md == SALF_FIELD_EXP) return launch_fm<SALF_F32, SALF_FIELD_EXP>(P, dump, st);
+  if (dt == SALF_F32 && md == SALF_FIELD_SDF) return launch_fm<SALF_F32, SALF_FIELD_SDF>(P, dump, st);
+  if (dt == SALF_BF16 && md == SALF_FIELD_EXP) return launch_fm<SALF_BF16, SALF_FIELD_EXP>(P, dump, st);
+  return launch_fm<SALF_BF16, SALF_FIELD_SDF>(P, dump, st);
+}

@@ -1,0 +1,138 @@
+// salf_internal.h -- structures shared by the host runtime and the sm_103a
+// kernels of libsalf.  Not part of the public ABI (include/salf.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/salf.h"
+
+#define SALF_MAX_MASK_LEVELS 12
+#define SALF_MAX_BATCH 24
+#define SALF_TILE_W 8
+#define SALF_TILE_H 4
+#define SALF_WARPS_PER_BLOCK 8
+
+// Device status-word bits.
+#define SALF_DEVERR_STEP_CAP 1  // a traversal loop reached its iteration bound
+#define SALF_DEVERR_SDF_AB 2    // an SDF record has a <= 0 or b <= 0
+
+// Read-only view of a built scene, passed to kernels by value.
+//
+// Acceleration structure (replaces the paper's pointer octree, Sec. III-B):
+//  * occupancy pyramid: mask level 0 has one 64-bit word per 4x4x4 block of
+//    level-0 cells (bit = Morton index of the cell inside the block) plus the
+//    rank offset of the block's first occupied cell in `entries`; mask level
+//    m >= 1 has one word per 4x4x4 words of level m-1 (bit set iff that word
+//    is non-zero).  An empty cell is skipped together with the largest empty
+//    aligned pyramid cell that contains it (one slab exit per skip).
+//  * entries[rank] for each occupied level-0 cell: a voxel index (>= 0) or
+//    -2 - node for a subdivided cell; nodes hold 8 children with the same
+//    encoding (-1 = empty child).
+//  * params: records in Morton order of the voxel's min corner (FP32 or BF16);
+//    order[internal] = input index.
+struct DevScene {
+  const uint4* mask0;
+  const unsigned long long* mask[SALF_MAX_MASK_LEVELS];
+  int mdim[SALF_MAX_MASK_LEVELS][3];
+  const int* entries;
+  const int* nodes;
+  const void* params;
+  const int* order;
+  int* status;
+  double origin[3];
+  double inv_sfin;  // finest cells per metre
+  int K;
+  int M;
+  int Gf[3];
+  int mode, dtype;
+  int n;
+};
+
+// One render request as the kernels see it (prepared on the host in FP64).
+struct ReqDev {
+  int kind, W, H;
+  int moving;          // 1: per-ray pose (rolling-shutter camera or LiDAR with t1 > t0)
+  float inv_fx, inv_fy, cx, cy;
+  float half_fov, elev_min, elev_max, elev_step;
+  float R0[9];         // rotation at t0
+  float q0[4], q1[4];  // rotations at t0, t1 as unit quaternions (w, x, y, z), same hemisphere
+  float theta, inv_sin_theta;  // slerp angle between q0 and q1 (theta < 1e-4: normalised lerp)
+  int Oi[3];           // sensor origin at t0 in finest-cell units: Oi + Of
+  float Of[3];
+  float dO[3];         // origin(t1) - origin(t0), finest-cell units
+  float t_near, t_far; // metres; t_far = +inf if unbounded
+  float time0, time1;  // t0, t1 (only for the debug ray dump)
+  const float* rays;   // explicit rays (device)
+  // outputs
+  float* rgb;
+  float* depth;
+  float* opacity;
+  float* intensity;
+  float* saved;
+  unsigned char* valid;
+  int* vcount;
+  int* visits;
+  int vcap;
+  float* ray_dump;
+  float t_min;
+  float bg[3];
+  int want_int;
+  // tiling
+  int tiles_x;
+  int tile_w, tile_h;
+  int tile_begin, n_tiles;
+  // backward inputs (unused by the forward kernel)
+  const float* bsaved;
+  const float* g_rgb;
+  const float* g_depth;
+  const float* g_opacity;
+  const float* g_int;
+  float* d_params;
+};
+
+struct LaunchParams {
+  DevScene S;
+  int n_req;
+  int total_tiles;
+  ReqDev req[SALF_MAX_BATCH];
+};
+
+// ---------------------------------------------------------------- host side
+
+struct salf_ctx {
+  int device;
+};
+
+struct salf_scene {
+  salf_ctx* ctx = nullptr;
+  int device = 0;
+  DevScene dev{};
+  int64_t n = 0;
+  int32_t mode = 0, dtype = 0, K = 0;
+  int32_t dims[3] = {0, 0, 0};
+  double origin[3] = {0, 0, 0};
+  double s0 = 0, sfin = 0;
+  int64_t n_cells0 = 0, n_nodes = 0, device_bytes = 0;
+  std::vector<void*> allocations;  // every device buffer the scene owns
+  // staging for host-memory outputs / explicit rays (grown on demand)
+  std::mutex staging_mu;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+};
+
+// Implemented in the .cu / .cpp files of the library.
+void salf_set_error(const std::string& msg);
+salf_status salf_cuda_fail(cudaError_t e, const char* what);
+salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_scene** out);
+salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* sen,
+                                 const salf_render_opts* opts, ReqDev* r);
+int64_t salf_request_rays(const salf_sensor* sen);
+cudaError_t salf_launch_gather_params(const float* in, const int* order, void* out, int64_t n,
+                                      int dtype, int mode, int* status, cudaStream_t st);
+cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st);
+cudaError_t salf_launch_backward(const LaunchParams& P, cudaStream_t st);

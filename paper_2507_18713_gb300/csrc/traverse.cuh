@@ -1,0 +1,447 @@
+// traverse.cuh -- per-ray device code shared by the forward and adjoint
+// kernels: sensor ray generation (Fig. 2, Sec. V-C), traversal of the sparse
+// voxel structure (Sec. III-B), record loads and the local fields of
+// Eq. 1, 2, 5, 6.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "salf_internal.h"
+
+namespace salf {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kSH0 = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+constexpr float kSH1 = 0.48860251190291992f;  // sqrt(3) / (2 sqrt(pi))
+
+struct Ray {
+  int Oi[3];     // origin, finest-cell units: Oi + Of
+  float Of[3];
+  float d[3];    // unit direction, world frame
+  float tn, tf;  // metres
+  float s;       // time fraction (t - t0) / (t1 - t0) of the ray's pose
+  bool valid;
+};
+
+__device__ __forceinline__ void quat_to_mat(const float q[4], float R[9]) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Sensor ray of pixel (u, v) / LiDAR (azimuth u, beam v).
+__device__ __forceinline__ void gen_ray(const ReqDev& Q, const DevScene& S, int u, int v,
+                                        int ray, Ray& r) {
+  r.valid = true;
+  if (Q.kind == SALF_RAYS_EXPLICIT) {
+    const float4* q = reinterpret_cast<const float4*>(Q.rays) + 2 * (size_t)ray;
+    float4 a = __ldg(q), b = __ldg(q + 1);
+    double o[3] = {(double)a.x, (double)a.y, (double)a.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double g = (o[k] - S.origin[k]) * S.inv_sfin;
+      double f = floor(g);
+      r.Oi[k] = (int)f;
+      r.Of[k] = (float)(g - f);
+    }
+    float dx = a.w, dy = b.x, dz = b.y;
+    float nn = dx * dx + dy * dy + dz * dz;
+    r.valid = nn > 0.f;
+    float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
+    r.d[0] = dx * inv;
+    r.d[1] = dy * inv;
+    r.d[2] = dz * inv;
+    r.tn = b.z;
+    r.tf = b.w > 0.f ? b.w : __int_as_float(0x7f800000);
+    r.s = 0.f;
+    return;
+  }
+  float dc[3];
+  float s = 0.f;
+  if (Q.kind == SALF_LIDAR_SPIN) {
+    float e = Q.elev_max - (float)v * Q.elev_step;
+    float ph = (2.f * kPi) * ((float)u / (float)Q.W);
+    float se, ce, sp, cp;
+    sincosf(e, &se, &ce);
+    sincosf(ph, &sp, &cp);
+    dc[0] = ce * cp;
+    dc[1] = ce * sp;
+    dc[2] = se;
+    if (Q.moving) s = (float)u / (float)Q.W;
+  } else {
+    float px = (float)u + 0.5f, py = (float)v + 0.5f;
+    if (Q.kind == SALF_PINHOLE) {
+      dc[0] = (px - Q.cx) * Q.inv_fx;
+      dc[1] = (py - Q.cy) * Q.inv_fy;
+      dc[2] = 1.f;
+    } else if (Q.kind == SALF_FISHEYE_EQUIDIST) {
+      float mx = (px - Q.cx) * Q.inv_fx, my = (py - Q.cy) * Q.inv_fy;
+      float th = sqrtf(mx * mx + my * my);
+      r.valid = th <= Q.half_fov;
+      float st, ct;
+      sincosf(th, &st, &ct);
+      float k = th > 0.f ? st / th : 1.f;
+      dc[0] = k * mx;
+      dc[1] = k * my;
+      dc[2] = ct;
+    } else {  // equirectangular panorama
+      float lon = (2.f * kPi) * (px / (float)Q.W - 0.5f);
+      float lat = Q.elev_max - (py / (float)Q.H) * (Q.elev_max - Q.elev_min);
+      float sl, cl, sa, ca;
+      sincosf(lon, &sl, &cl);
+      sincosf(lat, &sa, &ca);
+      dc[0] = ca * sl;
+      dc[1] = -sa;
+      dc[2] = ca * cl;
+    }
+    if (Q.moving) s = (float)v / (float)(Q.H - 1);
+  }
+  float R[9];
+  if (s > 0.f) {
+    float q[4];
+    if (Q.theta > 1e-4f) {
+      float a = sinf((1.f - s) * Q.theta) * Q.inv_sin_theta;
+      float b = sinf(s * Q.theta) * Q.inv_sin_theta;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[k] = a * Q.q0[k] + b * Q.q1[k];
+    } else {
+      float nn = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        q[k] = (1.f - s) * Q.q0[k] + s * Q.q1[k];
+        nn += q[k] * q[k];
+      }
+      float inv = rsqrtf(nn);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[k] *= inv;
+    }
+    quat_to_mat(q, R);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = Q.R0[k];
+  }
+  float d0 = R[0] * dc[0] + R[1] * dc[1] + R[2] * dc[2];
+  float d1 = R[3] * dc[0] + R[4] * dc[1] + R[5] * dc[2];
+  float d2 = R[6] * dc[0] + R[7] * dc[1] + R[8] * dc[2];
+  float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  r.d[0] = d0 * inv;
+  r.d[1] = d1 * inv;
+  r.d[2] = d2 * inv;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r.Oi[k] = Q.Oi[k];
+    r.Of[k] = fmaf(s, Q.dO[k], Q.Of[k]);
+  }
+  r.tn = Q.t_near;
+  r.tf = Q.t_far;
+  r.s = s;
+}
+
+// Debug dump of a generated ray: world origin, unit direction, time, valid.
+__device__ __forceinline__ void dump_ray(const ReqDev& Q, const DevScene& S, const Ray& r, int ray) {
+  float* p = Q.ray_dump + 8 * (size_t)ray;
+  const double sf = 1.0 / S.inv_sfin;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    p[k] = (float)(S.origin[k] + ((double)r.Oi[k] + (double)r.Of[k]) * sf);
+    p[3 + k] = r.d[k];
+  }
+  p[6] = Q.time0 + r.s * (Q.time1 - Q.time0);
+  p[7] = r.valid ? 1.f : 0.f;
+}
+
+// Traversal state of one ray, all positions relative to the origin cell Oi so
+// that plane distances are small integers minus a fraction.
+struct Walk {
+  int Oi[3];
+  float Of[3];
+  float D[3];     // direction in finest cells per metre (zero components -> 1e-20)
+  float invD[3];  // metres per finest cell
+  int c[3];       // current finest cell
+  float t;        // entry distance of the current cell
+  float tend;     // min(t_far, root-box exit)
+  int steps, max_steps;
+  bool alive;
+};
+
+__device__ __forceinline__ void walk_init(const DevScene& S, const Ray& r, Walk& w) {
+  float isf = (float)S.inv_sfin;
+  float t0 = r.tn, t1 = r.tf;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    w.Oi[a] = r.Oi[a];
+    w.Of[a] = r.Of[a];
+    float D = r.d[a] * isf;
+    if (fabsf(D) < 1e-20f) D = 1e-20f;
+    w.D[a] = D;
+    w.invD[a] = 1.f / D;
+    float lo = ((float)(0 - r.Oi[a]) - r.Of[a]) * w.invD[a];
+    float hi = ((float)(S.Gf[a] - r.Oi[a]) - r.Of[a]) * w.invD[a];
+    t0 = fmaxf(t0, fminf(lo, hi));
+    t1 = fminf(t1, fmaxf(lo, hi));
+  }
+  w.alive = r.valid && (t0 < t1);
+  w.t = t0;
+  w.tend = t1;
+  w.steps = 0;
+  w.max_steps = S.Gf[0] + S.Gf[1] + S.Gf[2] + 64;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int q = r.Oi[a] + __float2int_rd(fmaf(t0, w.D[a], r.Of[a]));
+    w.c[a] = min(max(q, 0), S.Gf[a] - 1);
+  }
+}
+
+__device__ __forceinline__ unsigned morton6(unsigned x, unsigned y, unsigned z) {
+  return (x & 1u) | ((y & 1u) << 1) | ((z & 1u) << 2) | ((x & 2u) << 2) | ((y & 2u) << 3) |
+         ((z & 2u) << 4);
+}
+
+// Leaf of the structure containing finest cell (ix, iy, iz): a voxel
+// (returns its internal index) or an empty region (returns -1).  *ls = log2 of
+// the leaf's edge in finest cells.
+__device__ __forceinline__ int find_leaf(const DevScene& S, int ix, int iy, int iz, int* ls) {
+  const int K = S.K;
+  int cx = ix >> K, cy = iy >> K, cz = iz >> K;
+  int bx = cx >> 2, by = cy >> 2, bz = cz >> 2;
+  uint4 w = __ldg(&S.mask0[((size_t)bz * S.mdim[0][1] + by) * S.mdim[0][0] + bx]);
+  unsigned long long m = ((unsigned long long)w.y << 32) | (unsigned long long)w.x;
+  unsigned bit = morton6(cx & 3, cy & 3, cz & 3);
+  if ((m >> bit) & 1ull) {
+    int e = __ldg(&S.entries[w.z + __popcll(m & ((1ull << bit) - 1ull))]);
+    int l = K;
+    while (e <= -2) {
+      --l;
+      int ch = ((ix >> l) & 1) | (((iy >> l) & 1) << 1) | (((iz >> l) & 1) << 2);
+      e = __ldg(&S.nodes[(size_t)(-2 - e) * 8 + ch]);
+    }
+    *ls = l;
+    return e;
+  }
+  if ((m >> (bit & 0x38u)) & 0xffull) {
+    *ls = K;
+    return -1;
+  }
+  if (m) {
+    *ls = K + 1;
+    return -1;
+  }
+  int ux = bx, uy = by, uz = bz;
+  for (int lev = 1; lev < S.M; ++lev) {
+    unsigned long long mw = __ldg(
+        &S.mask[lev][((size_t)(uz >> 2) * S.mdim[lev][1] + (uy >> 2)) * S.mdim[lev][0] + (ux >> 2)]);
+    unsigned b = morton6(ux & 3, uy & 3, uz & 3);
+    if ((mw >> (b & 0x38u)) & 0xffull) {
+      *ls = K + 2 * lev;
+      return -1;
+    }
+    if (mw) {
+      *ls = K + 2 * lev + 1;
+      return -1;
+    }
+    ux >>= 2;
+    uy >>= 2;
+    uz >>= 2;
+  }
+  *ls = K + 2 * S.M;
+  return -1;
+}
+
+struct Hit {
+  int vox;
+  int base[3];
+  int ls;
+  float tin, tout;
+};
+
+// Advance `w` to the next voxel crossed with positive length.  Empty leaves
+// are skipped whole: the ray leaves a leaf box through the face of the
+// nearest exit plane, and the neighbour cell across that face is the next
+// point to locate (other coordinates from the exit point, kept inside the
+// face and never moved backwards, so every hop makes progress).
+__device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h) {
+  while (w.alive) {
+    int ls;
+    int vox = find_leaf(S, w.c[0], w.c[1], w.c[2], &ls);
+    const int E = 1 << ls;
+    int b[3];
+    float tx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b[a] = w.c[a] & ~(E - 1);
+      int p = (w.D[a] > 0.f ? b[a] + E : b[a]) - w.Oi[a];
+      tx[a] = ((float)p - w.Of[a]) * w.invD[a];
+    }
+    int ax = (tx[0] <= tx[1] && tx[0] <= tx[2]) ? 0 : (tx[1] <= tx[2] ? 1 : 2);
+    float te = tx[ax];
+    bool found = false;
+    if (vox >= 0) {
+      float tin = w.t;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int p = (w.D[a] > 0.f ? b[a] : b[a] + E) - w.Oi[a];
+        tin = fmaxf(tin, ((float)p - w.Of[a]) * w.invD[a]);
+      }
+      float tout = fminf(te, w.tend);
+      if (tout > tin) {
+        h.vox = vox;
+        h.ls = ls;
+        h.base[0] = b[0];
+        h.base[1] = b[1];
+        h.base[2] = b[2];
+        h.tin = tin;
+        h.tout = tout;
+        found = true;
+      }
+    }
+    // hop to the neighbour across the exit face
+    if (!(te < w.tend) || ++w.steps > w.max_steps) {
+      if (w.steps > w.max_steps) atomicOr(S.status, SALF_DEVERR_STEP_CAP);
+      w.alive = false;
+    } else {
+      int nc[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (a == ax) {
+          nc[a] = w.D[a] > 0.f ? b[a] + E : b[a] - 1;
+        } else {
+          int q = w.Oi[a] + __float2int_rd(fmaf(te, w.D[a], w.Of[a]));
+          q = min(max(q, b[a]), b[a] + E - 1);
+          q = min(max(q, 0), S.Gf[a] - 1);
+          nc[a] = w.D[a] > 0.f ? max(q, w.c[a]) : min(q, w.c[a]);
+        }
+      }
+      if (nc[ax] < 0 || nc[ax] >= S.Gf[ax]) w.alive = false;
+      w.c[0] = nc[0];
+      w.c[1] = nc[1];
+      w.c[2] = nc[2];
+      w.t = fmaxf(w.t, te);
+    }
+    if (found) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- records
+
+template <int DT>
+struct Record;
+
+// FP32: 32 floats (128 B).  Loads what the field needs: floats 0..27 always
+// (W_sigma/W_s, W_c, W_sh, a, b), 28..31 only with intensity.
+template <>
+struct Record<SALF_F32> {
+  float v[32];
+  __device__ __forceinline__ void load(const void* base, int vox, bool intensity) {
+    const float4* p = reinterpret_cast<const float4*>(base) + (size_t)vox * 8;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      float4 q = __ldg(p + k);
+      v[4 * k] = q.x;
+      v[4 * k + 1] = q.y;
+      v[4 * k + 2] = q.z;
+      v[4 * k + 3] = q.w;
+    }
+    if (intensity) {
+      float4 q = __ldg(p + 7);
+      v[28] = q.x;
+      v[29] = q.y;
+      v[30] = q.z;
+      v[31] = q.w;
+    } else {
+      v[28] = v[29] = v[30] = v[31] = 0.f;
+    }
+  }
+};
+
+// BF16: 32 bf16 (64 B), widened to FP32 in registers.
+template <>
+struct Record<SALF_BF16> {
+  float v[32];
+  __device__ __forceinline__ void load(const void* base, int vox, bool intensity) {
+    const uint4* p = reinterpret_cast<const uint4*>(base) + (size_t)vox * 4;
+    (void)intensity;  // every 16-byte chunk holds a used scalar
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint4 q = __ldg(p + k);
+      unsigned w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        v[8 * k + 2 * j] = __uint_as_float(w4[j] << 16);
+        v[8 * k + 2 * j + 1] = __uint_as_float(w4[j] & 0xffff0000u);
+      }
+    }
+  }
+};
+
+// Local coordinates of the segment midpoint inside the voxel box
+// [base, base + 2^ls) (finest cells): x = (p - centre) / (edge / 2).
+__device__ __forceinline__ void local_coords(const Walk& w, const Hit& h, float tm, float x[3]) {
+  const float E = (float)(1 << h.ls);
+  const float inv_half = 2.f / E;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float p = fmaf(tm, w.D[a], w.Of[a]);  // relative to the origin cell
+    float ctr = (float)(h.base[a] - w.Oi[a]) + 0.5f * E;
+    x[a] = (p - ctr) * inv_half;
+  }
+}
+
+__device__ __forceinline__ float sigmoidf_fast(float z) {
+  return __fdividef(1.f, 1.f + __expf(-z));
+}
+
+// Eq. 1 (EXP) or Eq. 5-6 (SDF) density at x; `lin` = W . [x, 1].
+template <int MODE>
+__device__ __forceinline__ float density(const float* rec, const float x[3], float* lin) {
+  float s = fmaf(rec[0], x[0], fmaf(rec[1], x[1], fmaf(rec[2], x[2], rec[3])));
+  *lin = s;
+  if (MODE == SALF_FIELD_EXP) return __expf(s);
+  float a = rec[25], b = rec[26];
+  float e = __expf(-fabsf(s) / b);
+  float sg = (s > 0.f) ? 1.f : ((s < 0.f) ? -1.f : 0.f);
+  return 0.5f * a + 0.5f * a * sg * (1.f - e);
+}
+
+// Eq. 2 colour: c = sigmoid(W_c x + W_sh gamma(d)).
+__device__ __forceinline__ void colour(const float* rec, const float x[3], const float gam[4],
+                                       float c[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float z = rec[4 + 3 * r] * x[0] + rec[5 + 3 * r] * x[1] + rec[6 + 3 * r] * x[2];
+    z = fmaf(rec[13 + 4 * r], gam[0], z);
+    z = fmaf(rec[14 + 4 * r], gam[1], z);
+    z = fmaf(rec[15 + 4 * r], gam[2], z);
+    z = fmaf(rec[16 + 4 * r], gam[3], z);
+    c[r] = sigmoidf_fast(z);
+  }
+}
+
+__device__ __forceinline__ float intensity_field(const float* rec, const float x[3]) {
+  float z = fmaf(rec[27], x[0], fmaf(rec[28], x[1], fmaf(rec[29], x[2], rec[30])));
+  return sigmoidf_fast(z);
+}
+
+__device__ __forceinline__ void sh_basis(const float d[3], float gam[4]) {
+  gam[0] = kSH0;
+  gam[1] = kSH1 * d[1];
+  gam[2] = kSH1 * d[2];
+  gam[3] = kSH1 * d[0];
+}
+
+// Warp tile -> request, pixel.
+__device__ __forceinline__ int find_request(const LaunchParams& P, int warp) {
+  int r = 0;
+  while (r + 1 < P.n_req && warp >= P.req[r + 1].tile_begin) ++r;
+  return r;
+}
+
+}  // namespace salf

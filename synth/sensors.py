@@ -88,10 +88,11 @@ def lidar(beams, azimuths, pose0, pose1=None, t0=0.0, t1=0.1, elev_min_deg=-25.0
     return s
 
 
-def explicit_rays(rays: np.ndarray):
-    """Caller-given rays: (R, 8) float32 rows (ox, oy, oz, dx, dy, dz, t_near, t_far);
-    t_far <= 0 means unbounded."""
-    rays = np.ascontiguousarray(rays, dtype=np.float32).reshape(-1, 8)
+def explicit_rays(rays: np.ndarray, dtype=np.float32):
+    """Caller-given rays: (R, 8) rows (ox, oy, oz, dx, dy, dz, t_near, t_far);
+    t_far <= 0 means unbounded.  float32 (what the renderer takes) or float64
+    (accepted by the oracle only)."""
+    rays = np.ascontiguousarray(rays, dtype=dtype).reshape(-1, 8)
     s = _base("explicit", rays.shape[0], 1, np.eye(3, 4))
     s["rays"] = rays
     return s
