@@ -167,6 +167,7 @@ typedef struct {
  *   visit_count, visits: see salf_render_opts.visits_cap
  *   ray_dump  R x 8 (debugging aid): the generated ray as (ox, oy, oz, dx, dy,
  *             dz, time, valid) in world coordinates
+ *   steps     R (debugging aid): structure leaves the traversal stepped through
  * on_host = 0: device pointers; on_host = 1: host pointers (the library renders
  * into its own device staging buffers and copies back before returning).
  */
@@ -180,6 +181,7 @@ typedef struct {
   int32_t* visit_count;
   int32_t* visits;
   float* ray_dump;
+  int32_t* steps;
   int32_t on_host;
 } salf_outputs;
 

@@ -85,7 +85,7 @@ def _load():
             lib.orc_field.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             lib.orc_trace.argtypes = [vp, vp, vp, dp, dp, i32, vp, i64]
             lib.orc_trace.restype = i64
-            lib.orc_trace_eps.argtypes = [vp, vp, vp, dp, dp, dp, dp, i32, vp, i64]
+            lib.orc_trace_eps.argtypes = [vp, vp, vp, dp, dp, dp, dp, i32, vp, vp, vp, i64]
             lib.orc_trace_eps.restype = i64
             lib.orc_render.argtypes = [vp, C.POINTER(_Sensor), C.POINTER(_Opts), vp, i64,
                                        C.POINTER(_Outputs)]
@@ -232,13 +232,23 @@ def trace(oscene, o, d, t_near=0.0, t_far=np.inf, brute_force=False, cap=1 << 16
     return [(hits[i].voxel, hits[i].t_in, hits[i].t_out) for i in range(min(n, cap))]
 
 
-def trace_eps(oscene, o, d, t_near, t_far, eps_abs, eps_rel, sign, cap=1 << 16):
+def trace_eps(oscene, o, d, t_near, t_far, eps_abs, eps_rel, sign, cap=1 << 16,
+              intervals=False):
+    """Voxels hit when every box is grown (sign=+1) / shrunk (-1) by
+    eps_abs + eps_rel * distance; ids sorted by entry (and the perturbed
+    [t_in, t_out] per id if intervals)."""
     o = np.ascontiguousarray(o, dtype=np.float64)
     d = np.ascontiguousarray(d, dtype=np.float64)
     ids = np.zeros(cap, np.int32)
+    ti = np.zeros(cap)
+    to = np.zeros(cap)
     n = _load().orc_trace_eps(oscene._h, _ptr(o), _ptr(d), float(t_near), float(t_far),
-                              float(eps_abs), float(eps_rel), int(sign), _ptr(ids), cap)
-    return ids[:min(n, cap)].tolist()
+                              float(eps_abs), float(eps_rel), int(sign), _ptr(ids), _ptr(ti),
+                              _ptr(to), cap)
+    n = min(n, cap)
+    if intervals:
+        return ids[:n].tolist(), ti[:n], to[:n]
+    return ids[:n].tolist()
 
 
 def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),

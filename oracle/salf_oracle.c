@@ -360,7 +360,7 @@ int64_t orc_trace(const orc_scene* s, const double o[3], const double d[3], doub
 
 int64_t orc_trace_eps(const orc_scene* s, const double o[3], const double d[3], double tn,
                       double tf, double eps_abs, double eps_rel, int32_t sign, int32_t* ids,
-                      int64_t cap) {
+                      double* t_in, double* t_out, int64_t cap) {
   ivec cand = {0, 0, 0};
   if (s->n <= 20000) {
     for (int64_t v = 0; v < s->n; ++v) iv_push(&cand, (int32_t)v);
@@ -386,7 +386,11 @@ int64_t orc_trace_eps(const orc_scene* s, const double o[3], const double d[3], 
       hv_push(&hv, v, a, b);
   }
   sort_hits(&hv, tn);
-  for (int64_t i = 0; i < hv.n && i < cap; ++i) ids[i] = hv.h[i].voxel;
+  for (int64_t i = 0; i < hv.n && i < cap; ++i) {
+    ids[i] = hv.h[i].voxel;
+    if (t_in) t_in[i] = hv.h[i].t_in;
+    if (t_out) t_out[i] = hv.h[i].t_out;
+  }
   int64_t n = hv.n;
   free(hv.h);
   free(cand.v);

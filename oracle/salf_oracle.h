@@ -98,10 +98,11 @@ void orc_field(const double* rec, int32_t mode, const double x[3], const double 
 int64_t orc_trace(const orc_scene* s, const double o[3], const double d[3], double tn,
                   double tf, int32_t brute_force, orc_hit* hits, int64_t cap);
 /* Same, with every voxel box grown (sign=+1) or shrunk (sign=-1) by
- * eps = eps_abs + eps_rel * |box centre - o|; returns ids sorted by entry. */
+ * eps = eps_abs + eps_rel * |box centre - o|; returns ids sorted by entry and
+ * (if t_in / t_out are not NULL) the perturbed boxes' entry / exit. */
 int64_t orc_trace_eps(const orc_scene* s, const double o[3], const double d[3], double tn,
                       double tf, double eps_abs, double eps_rel, int32_t sign, int32_t* ids,
-                      int64_t cap);
+                      double* t_in, double* t_out, int64_t cap);
 
 int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
                const int64_t* idx, int64_t m, const orc_outputs* out);

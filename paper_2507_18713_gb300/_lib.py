@@ -48,7 +48,7 @@ class Outputs(C.Structure):
     _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("opacity", c_void_p),
                 ("intensity", c_void_p), ("saved", c_void_p), ("valid", c_void_p),
                 ("visit_count", c_void_p), ("visits", c_void_p), ("ray_dump", c_void_p),
-                ("on_host", c_int32)]
+                ("steps", c_void_p), ("on_host", c_int32)]
 
 
 class SceneInfo(C.Structure):

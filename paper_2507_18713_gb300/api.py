@@ -154,7 +154,8 @@ class Scene:
 
     def render(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
                visits_cap=0, outputs=("rgb", "depth", "opacity"), saved=False, valid=True,
-               stream=None, out: dict | None = None, ray_dump: bool = False) -> dict:
+               stream=None, out: dict | None = None, ray_dump: bool = False,
+               steps: bool = False) -> dict:
         """salf_render_rays into (new or given) CUDA tensors; asynchronous on
         `stream` (default: torch's current stream)."""
         R = n_rays(sensor)
@@ -174,8 +175,10 @@ class Scene:
         o = L.Outputs()
         if ray_dump and "ray_dump" not in res:
             res["ray_dump"] = torch.empty((R, 8), dtype=torch.float32, device=dev)
+        if steps and "steps" not in res:
+            res["steps"] = torch.empty((R,), dtype=torch.int32, device=dev)
         for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits",
-                  "ray_dump"):
+                  "ray_dump", "steps"):
             if k in res:
                 setattr(o, k, res[k].data_ptr())
         keep: list = []

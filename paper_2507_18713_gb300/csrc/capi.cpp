@@ -297,7 +297,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
   }
   const salf_render_opts o = opts ? *opts : default_opts();
   if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
-      !(o.visits_cap > 0 && out->visits) && !out->ray_dump) {
+      !(o.visits_cap > 0 && out->visits) && !out->ray_dump && !out->steps) {
     g_err = "salf_render_rays: no output requested";
     return SALF_ERR_INVALID;
   }
@@ -305,8 +305,8 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
     g_err = "salf_render_rays: visits_cap > 0 needs visits and visit_count";
     return SALF_ERR_INVALID;
   }
-  if (out->on_host && out->ray_dump) {
-    g_err = "salf_render_rays: ray_dump needs device outputs";
+  if (out->on_host && (out->ray_dump || out->steps)) {
+    g_err = "salf_render_rays: ray_dump and steps need device outputs";
     return SALF_ERR_INVALID;
   }
   if (!out->on_host && misaligned(out->saved, 16)) {
@@ -336,6 +336,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
     r.vcount = out->visit_count;
     r.visits = out->visits;
     r.ray_dump = out->ray_dump;
+    r.steps_out = out->steps;
     if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
     return SALF_OK;
   }

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) k_forward(const __grid_constant__ LaunchP
   }
   if (Q.valid) Q.valid[ray] = valid ? 1 : 0;
   if (DUMP) {
+    if (Q.steps_out) Q.steps_out[ray] = w.steps;
     if (Q.vcap > 0) {
       Q.vcount[ray] = nvis;
       for (int k = nvis; k < Q.vcap; ++k) Q.visits[(size_t)ray * Q.vcap + k] = -1;
@@ -115,7 +116,7 @@ static cudaError_t launch_fm(const LaunchParams& P, bool dump, cudaStream_t st) 
 
 cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
   bool dump = false;
-  for (int i = 0; i < P.n_req; ++i) dump = dump || P.req[i].vcap > 0 || P.req[i].ray_dump;
+  for (int i = 0; i < P.n_req; ++i) dump = dump || P.req[i].vcap > 0 || P.req[i].ray_dump || P.req[i].steps_out;
   const int dt = P.S.dtype, md = P.S.mode;
   if (dt == SALF_F32 && md == SALF_FIELD_EXP) return launch_fm<SALF_F32, SALF_FIELD_EXP>(P, dump, st);
   if (dt == SALF_F32 && md == SALF_FIELD_SDF) return launch_fm<SALF_F32, SALF_FIELD_SDF>(P, dump, st);

@@ -79,6 +79,7 @@ struct ReqDev {
   int* visits;
   int vcap;
   float* ray_dump;
+  int* steps_out;
   float t_min;
   float bg[3];
   int want_int;

@@ -117,10 +117,13 @@ def check_visits(oracle, osc, sensor, scene, g_vis, g_cnt, o_vis, o_cnt, idx):
         o, d = rays["o"][0], rays["d"][0]
         tn, tf = rays["t_near"][0], rays["t_far"][0]
         shrunk = oracle.trace_eps(osc, o, d, tn, tf, EPS_ABS_CELLS * sf, EPS_REL, -1)
-        grown = oracle.trace_eps(osc, o, d, tn, tf, EPS_ABS_CELLS * sf, EPS_REL, +1)
+        grown, g_in, g_out = oracle.trace_eps(osc, o, d, tn, tf, EPS_ABS_CELLS * sf, EPS_REL, +1,
+                                              intervals=True)
         gl = [int(v) for v in g_vis[b][:g_cnt[b]]]
         assert set(shrunk) <= set(gl) <= set(grown), (ray_id, gl, shrunk, grown)
+        # order: two voxels whose grown intervals overlap may come either way
+        # (entered within eps of the same point); otherwise the earlier first
         pos = {v: i for i, v in enumerate(grown)}
-        order = [pos[v] for v in gl]
-        assert order == sorted(order), (ray_id, gl, grown)
+        for a, c in zip(gl, gl[1:]):
+            assert g_in[pos[a]] <= g_out[pos[c]], (ray_id, gl, grown)
     return len(g_cnt), len(bad)
