@@ -230,6 +230,30 @@ salf_status salf_render_rays(salf_scene* scene, const salf_sensor* sensor,
                              void* stream);
 
 /*
+ * salf_render_rays for host output buffers, without any device allocation.
+ * The paper has no counterpart: this serves callers that cannot let a library
+ * allocate device memory -- real-time loops that cannot absorb an
+ * allocation's latency and implicit synchronisation, applications whose
+ * device memory is reserved up front by their own pooling allocator, and
+ * plug-ins whose host forbids them to allocate.  (salf_render_rays with
+ * on_host = 1 grows a staging buffer with cudaMalloc instead.)
+ * The outputs are staged in a fixed 48 MiB array compiled into the library
+ * (every device that loads the library holds it until the process exits);
+ * requests whose outputs need more staging than that are rejected with
+ * SALF_ERR_INVALID.  `out` holds host pointers (on_host is ignored); the
+ * debug outputs (visits, visit_count, ray_dump, steps) are not supported;
+ * explicit rays must be device memory.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Calls on one device share
+ * the array: two calls that overlap on the GPU (e.g. from two host threads)
+ * race, so serialise them.  Synchronous: returns after the outputs are in the
+ * host buffers.  Calls no cudaMalloc, cudaFree or allocating routine.
+ */
+salf_status salf_render_rays_host_noalloc(salf_scene* scene, const salf_sensor* sensor,
+                                          const salf_render_opts* opts,
+                                          const salf_outputs* out, void* stream);
+
+/*
  * Adjoint of salf_render_rays (gradients of Eq. 1-6 compositing, transmittance
  * recomputed front to back).  `saved` is the R x 8 array the forward call wrote
  * with the same scene, sensor and options.  d_rgb (R x 3), d_depth,

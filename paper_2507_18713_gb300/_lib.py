@@ -73,6 +73,8 @@ SIGNATURES = {
     "salf_scene_update_params": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
     "salf_render_rays": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts), C.POINTER(Outputs),
                           c_void_p], c_int32),
+    "salf_render_rays_host_noalloc": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),
+                                       C.POINTER(Outputs), c_void_p], c_int32),
     "salf_render_backward": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts), c_void_p,
                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "salf_scene_check": ([c_void_p], c_int32),

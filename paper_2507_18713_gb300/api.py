@@ -210,6 +210,27 @@ class Scene:
                                           _stream_ptr(stream)), "salf_render_rays(host)")
         return res
 
+    def render_host_noalloc(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                            want_intensity=False, outputs=("rgb", "depth", "opacity"), out=None,
+                            stream=None) -> dict:
+        """salf_render_rays_host_noalloc: like render_host, but the library
+        stages the outputs in its fixed device array instead of allocating."""
+        R = n_rays(sensor)
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,), "valid": (R,)}
+        res = out if out is not None else {
+            k: torch.empty(shapes[k], dtype=torch.uint8 if k == "valid" else torch.float32)
+            for k in outputs}
+        o = L.Outputs()
+        for k, v in res.items():
+            setattr(o, k, v.data_ptr())
+        keep: list = []
+        s = sensor_struct(sensor, keep)
+        op = opts_struct(t_min, background, want_intensity, 0)
+        L.check(L.load().salf_render_rays_host_noalloc(self._h, C.byref(s), C.byref(op),
+                                                       C.byref(o), _stream_ptr(stream)),
+                "salf_render_rays_host_noalloc")
+        return res
+
     def backward(self, sensor: dict, saved, d_rgb=None, d_depth=None, d_opacity=None,
                  d_intensity=None, d_params=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
                  want_intensity=False, stream=None):
