@@ -64,10 +64,11 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ Launch
   float T = 1.f, Pk = 0.f;
   int k = 0;
 
+  const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   for (;;) {
     Hit h;
-    const bool hit = next_hit(S, w, h);
-    if (!__any_sync(0xffffffffu, hit)) break;
+    const bool hit = next_hit(S, w, h, budget);
+    if (!__any_sync(0xffffffffu, hit || w.alive)) break;
     if (hit) {
       Record<DT> rec;
       rec.load(S.params, h.vox, want_int);

@@ -2,6 +2,7 @@
 // context, scene lifetime, request preparation (done in FP64 on the host),
 // render / adjoint dispatch, host-memory staging.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -187,6 +188,15 @@ static void mat_to_quat(const double* P, double q[4]) {
   for (int k = 0; k < 4; ++k) q[k] /= nn;
 }
 
+int salf_step_budget() {
+  static const int budget = [] {
+    const char* e = std::getenv("SALF_STEP_BUDGET");
+    const int v = e ? std::atoi(e) : 0;
+    return v > 0 ? v : 1;
+  }();
+  return budget;
+}
+
 int64_t salf_request_rays(const salf_sensor* sen) {
   return (int64_t)sen->width * (int64_t)sen->height;
 }
@@ -323,6 +333,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
   salf_status st = salf_prepare_request(sc, sen, &o, &r);
   if (st != SALF_OK) return st;
   P.total_tiles = r.n_tiles;
+  P.step_budget = salf_step_budget();
   const size_t R = (size_t)salf_request_rays(sen);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
 
@@ -425,6 +436,7 @@ extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* s
   r.g_int = d_intensity;
   r.d_params = d_params;
   P.total_tiles = r.n_tiles;
+  P.step_budget = salf_step_budget();
   if ((e = salf_launch_backward(P, static_cast<cudaStream_t>(stream))) != cudaSuccess)
     return salf_cuda_fail(e, "backward launch");
   return SALF_OK;

@@ -120,6 +120,7 @@ extern "C" salf_status salf_render_rays_host_noalloc(salf_scene* sc, const salf_
   r.saved = out->saved ? reinterpret_cast<float*>(base + off[4]) : nullptr;
   r.valid = out->valid ? reinterpret_cast<unsigned char*>(base + off[5]) : nullptr;
   P.total_tiles = r.n_tiles;
+  P.step_budget = salf_step_budget();
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
   void* dst[6] = {out->rgb, out->depth, out->opacity, out->intensity, out->saved, out->valid};

@@ -12,10 +12,16 @@
 // has a hit (ballot).  Lanes whose ray terminated early idle in the ballot.
 #include "traverse.cuh"
 
+// Resident 256-thread blocks per SM the forward kernel is compiled for
+// (bounds its registers per thread).
+#ifndef SALF_FWD_MIN_BLOCKS
+#define SALF_FWD_MIN_BLOCKS 2
+#endif
+
 using namespace salf;
 
 template <int DT, int MODE, bool DUMP>
-__global__ void __launch_bounds__(256) k_forward(const __grid_constant__ LaunchParams P) {
+__global__ void __launch_bounds__(256, SALF_FWD_MIN_BLOCKS) k_forward(const __grid_constant__ LaunchParams P) {
   const int warp = blockIdx.x * SALF_WARPS_PER_BLOCK + (threadIdx.x >> 5);
   if (warp >= P.total_tiles) return;
   const int lane = threadIdx.x & 31;
@@ -45,10 +51,11 @@ __global__ void __launch_bounds__(256) k_forward(const __grid_constant__ LaunchP
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dp = 0.f, Op = 0.f, Ip = 0.f;
   int nvis = 0;
 
+  const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   for (;;) {
     Hit h;
-    const bool hit = next_hit(S, w, h);
-    if (!__any_sync(0xffffffffu, hit)) break;
+    const bool hit = next_hit(S, w, h, budget);
+    if (!__any_sync(0xffffffffu, hit || w.alive)) break;
     if (hit) {
       Record<DT> rec;
       rec.load(S.params, h.vox, want_int);

@@ -12,6 +12,7 @@
 #include "../../include/salf.h"
 
 #define SALF_MAX_MASK_LEVELS 12
+#define SALF_MAX_COL_LEVELS 16
 #define SALF_MAX_BATCH 24
 #define SALF_TILE_W 8
 #define SALF_TILE_H 4
@@ -33,6 +34,11 @@
 //  * entries[rank] for each occupied level-0 cell: a voxel index (>= 0) or
 //    -2 - node for a subdivided cell; nodes hold 8 children with the same
 //    encoding (-1 = empty child).
+//  * column pyramid: for every footprint of 2^c x 2^c level-0 columns, a
+//    128-bit mask of the z-layers (layer = layer_cells level-0 cells high)
+//    that hold any voxel.  A ray in an empty layer of a footprint can jump to
+//    the nearest occupied layer in its direction of travel, or to the
+//    footprint's side, in one step.
 //  * params: records in Morton order of the voxel's min corner (FP32 or BF16);
 //    order[internal] = input index.
 struct DevScene {
@@ -41,6 +47,11 @@ struct DevScene {
   int mdim[SALF_MAX_MASK_LEVELS][3];
   const int* entries;
   const int* nodes;
+  const uint4* col[SALF_MAX_COL_LEVELS];  // column masks per level: (lo64, hi64) as uint4
+  int cdim[SALF_MAX_COL_LEVELS][2];
+  int CL;           // column levels
+  int layer_shift;  // log2(layer height in finest cells)
+  int n_layers;     // <= 128
   const void* params;
   const int* order;
   int* status;
@@ -100,6 +111,7 @@ struct LaunchParams {
   DevScene S;
   int n_req;
   int total_tiles;
+  int step_budget;  // structure steps per lane between warp-wide compositing rounds
   ReqDev req[SALF_MAX_BATCH];
 };
 
@@ -133,6 +145,9 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
 salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* sen,
                                  const salf_render_opts* opts, ReqDev* r);
 int64_t salf_request_rays(const salf_sensor* sen);
+// Structure steps per lane between warp-wide compositing rounds (environment
+// override SALF_STEP_BUDGET, read once).
+int salf_step_budget();
 cudaError_t salf_launch_gather_params(const float* in, const int* order, void* out, int64_t n,
                                       int dtype, int mode, int* status, cudaStream_t st);
 cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st);

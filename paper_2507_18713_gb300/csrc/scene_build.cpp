@@ -224,6 +224,42 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
     }
   }
 
+  // ---- column pyramid: z-layer occupancy per footprint of 2^c x 2^c columns
+  int layer_cells = 1;
+  while ((d->dims[2] + layer_cells - 1) / layer_cells > 128) layer_cells *= 2;
+  const int n_layers = (d->dims[2] + layer_cells - 1) / layer_cells;
+  int cdim[SALF_MAX_COL_LEVELS][2];
+  cdim[0][0] = d->dims[0];
+  cdim[0][1] = d->dims[1];
+  std::vector<std::vector<uint4>> cols(1);
+  cols[0].assign((size_t)cdim[0][0] * cdim[0][1], make_uint4(0, 0, 0, 0));
+  for (int64_t p = 0; p < n; ++p) {
+    const int32_t v = order[p];
+    const int l = d->level[v];
+    const int64_t cx = d->ijk[3 * v] >> l, cy = d->ijk[3 * v + 1] >> l, cz = d->ijk[3 * v + 2] >> l;
+    const int layer = (int)(cz / layer_cells);
+    uint4& m = cols[0][(size_t)cy * cdim[0][0] + cx];
+    unsigned* wds = &m.x;
+    wds[layer >> 5] |= 1u << (layer & 31);
+  }
+  int CL = 1;
+  while ((cdim[CL - 1][0] > 1 || cdim[CL - 1][1] > 1) && CL < SALF_MAX_COL_LEVELS) {
+    cdim[CL][0] = (cdim[CL - 1][0] + 1) / 2;
+    cdim[CL][1] = (cdim[CL - 1][1] + 1) / 2;
+    std::vector<uint4> cur((size_t)cdim[CL][0] * cdim[CL][1], make_uint4(0, 0, 0, 0));
+    for (int64_t y = 0; y < cdim[CL - 1][1]; ++y)
+      for (int64_t x = 0; x < cdim[CL - 1][0]; ++x) {
+        const uint4 a = cols[CL - 1][(size_t)y * cdim[CL - 1][0] + x];
+        uint4& b = cur[(size_t)(y >> 1) * cdim[CL][0] + (x >> 1)];
+        b.x |= a.x;
+        b.y |= a.y;
+        b.z |= a.z;
+        b.w |= a.w;
+      }
+    cols.push_back(std::move(cur));
+    ++CL;
+  }
+
   // ---- device upload
   salf_scene* s = new salf_scene();
   Scope guard{s};
@@ -266,6 +302,20 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
   D.entries = dentries;
   D.nodes = dnodes;
   D.order = dorder;
+  for (int c = 0; c < CL; ++c) {
+    uint4* pc = nullptr;
+    if ((st = upload(s, cols[c], &pc)) != SALF_OK) return st;
+    D.col[c] = pc;
+    D.cdim[c][0] = cdim[c][0];
+    D.cdim[c][1] = cdim[c][1];
+  }
+  D.CL = CL;
+  {
+    int ls = 0;
+    while ((1 << ls) < layer_cells) ++ls;
+    D.layer_shift = ls + K;
+  }
+  D.n_layers = n_layers;
   void* status = nullptr;
   if ((st = dalloc(s, 16, &status)) != SALF_OK) return st;
   if ((ce = cudaMemset(status, 0, 16)) != cudaSuccess) return salf_cuda_fail(ce, "cudaMemset");

@@ -216,6 +216,7 @@ void scheduler(salf_server* s) {
       s->rays += r.rays;
     }
     P->total_tiles = tiles;
+    P->step_budget = salf_step_budget();
     s->stream_busy[idle]++;
     s->launches++;
     const bool inject = s->fail_launch_at > 0 && s->launches == s->fail_launch_at;

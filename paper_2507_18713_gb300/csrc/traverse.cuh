@@ -168,7 +168,8 @@ struct Walk {
   int c[3];       // current finest cell
   float t;        // entry distance of the current cell
   float tend;     // min(t_far, root-box exit)
-  int steps, max_steps;
+  int steps;
+  int cl;         // column-pyramid level to try next
   bool alive;
 };
 
@@ -192,7 +193,7 @@ __device__ __forceinline__ void walk_init(const DevScene& S, const Ray& r, Walk&
   w.t = t0;
   w.tend = t1;
   w.steps = 0;
-  w.max_steps = S.Gf[0] + S.Gf[1] + S.Gf[2] + 64;
+  w.cl = min(S.CL - 1, 6);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     int q = r.Oi[a] + __float2int_rd(fmaf(t0, w.D[a], r.Of[a]));
@@ -210,18 +211,18 @@ __device__ __forceinline__ unsigned morton6(unsigned x, unsigned y, unsigned z) 
 // the leaf's edge in finest cells.
 __device__ __forceinline__ int find_leaf(const DevScene& S, int ix, int iy, int iz, int* ls) {
   const int K = S.K;
-  int cx = ix >> K, cy = iy >> K, cz = iz >> K;
-  int bx = cx >> 2, by = cy >> 2, bz = cz >> 2;
-  uint4 w = __ldg(&S.mask0[((size_t)bz * S.mdim[0][1] + by) * S.mdim[0][0] + bx]);
-  unsigned long long m = ((unsigned long long)w.y << 32) | (unsigned long long)w.x;
-  unsigned bit = morton6(cx & 3, cy & 3, cz & 3);
+  const unsigned cx = (unsigned)ix >> K, cy = (unsigned)iy >> K, cz = (unsigned)iz >> K;
+  const unsigned bx = cx >> 2, by = cy >> 2, bz = cz >> 2;
+  const uint4 w = __ldg(&S.mask0[(bz * (unsigned)S.mdim[0][1] + by) * (unsigned)S.mdim[0][0] + bx]);
+  const unsigned long long m = ((unsigned long long)w.y << 32) | (unsigned long long)w.x;
+  const unsigned bit = morton6(cx & 3, cy & 3, cz & 3);
   if ((m >> bit) & 1ull) {
     int e = __ldg(&S.entries[w.z + __popcll(m & ((1ull << bit) - 1ull))]);
     int l = K;
     while (e <= -2) {
       --l;
-      int ch = ((ix >> l) & 1) | (((iy >> l) & 1) << 1) | (((iz >> l) & 1) << 2);
-      e = __ldg(&S.nodes[(size_t)(-2 - e) * 8 + ch]);
+      const int ch = ((ix >> l) & 1) | (((iy >> l) & 1) << 1) | (((iz >> l) & 1) << 2);
+      e = __ldg(&S.nodes[(unsigned)(-2 - e) * 8u + (unsigned)ch]);
     }
     *ls = l;
     return e;
@@ -234,11 +235,12 @@ __device__ __forceinline__ int find_leaf(const DevScene& S, int ix, int iy, int 
     *ls = K + 1;
     return -1;
   }
-  int ux = bx, uy = by, uz = bz;
+  unsigned ux = bx, uy = by, uz = bz;
   for (int lev = 1; lev < S.M; ++lev) {
-    unsigned long long mw = __ldg(
-        &S.mask[lev][((size_t)(uz >> 2) * S.mdim[lev][1] + (uy >> 2)) * S.mdim[lev][0] + (ux >> 2)]);
-    unsigned b = morton6(ux & 3, uy & 3, uz & 3);
+    const unsigned long long mw =
+        __ldg(&S.mask[lev][((uz >> 2) * (unsigned)S.mdim[lev][1] + (uy >> 2)) *
+                               (unsigned)S.mdim[lev][0] + (ux >> 2)]);
+    const unsigned b = morton6(ux & 3, uy & 3, uz & 3);
     if ((mw >> (b & 0x38u)) & 0xffull) {
       *ls = K + 2 * lev;
       return -1;
@@ -255,6 +257,71 @@ __device__ __forceinline__ int find_leaf(const DevScene& S, int ix, int iy, int 
   return -1;
 }
 
+// Column-pyramid skip at level `cl` from the current (empty) cell: the ray may
+// advance through every layer of the 2^cl x 2^cl-column footprint that holds
+// no voxel, up to the nearest occupied layer in its direction of travel or the
+// footprint's side.  Returns false if the current layer is occupied in the
+// footprint (no progress at this level).  Fills the skipped box [lo, hi)
+// (finest cells), its exit axis and exit distance.
+__device__ __forceinline__ bool col_skip(const DevScene& S, const Walk& w, int cl, float* t_exit,
+                                         int lo[3], int hi[3], int* axis) {
+  const int sh = S.K + cl;
+  const int F = 1 << sh;
+  const int fx = w.c[0] >> sh, fy = w.c[1] >> sh;
+  const int bx = fx << sh, by = fy << sh;
+  const float tx = ((float)((w.D[0] > 0.f ? bx + F : bx) - w.Oi[0]) - w.Of[0]) * w.invD[0];
+  const float ty = ((float)((w.D[1] > 0.f ? by + F : by) - w.Oi[1]) - w.Of[1]) * w.invD[1];
+  float te = fminf(tx, ty);
+  int ax = tx <= ty ? 0 : 1;
+  const bool up = w.D[2] > 0.f;
+  const int LS = S.layer_shift;
+  const int lcur = w.c[2] >> LS;
+  // furthest layer the ray reaches inside the footprint (widened toward travel)
+  const float zf = (float)w.Oi[2] + fmaf(fminf(te, w.tend), w.D[2], w.Of[2]) + (up ? 1e-3f : -1e-3f);
+  int lend = __float2int_rd(zf) >> LS;
+  lend = min(max(lend, 0), S.n_layers - 1);
+  const uint4 m = __ldg(&S.col[cl][(unsigned)fy * (unsigned)S.cdim[cl][0] + (unsigned)fx]);
+  const unsigned long long lo64 = ((unsigned long long)m.y << 32) | m.x;
+  const unsigned long long hi64 = ((unsigned long long)m.w << 32) | m.z;
+  int Ls;  // nearest occupied layer at or beyond lcur in the direction of travel
+  if (up) {
+    const unsigned long long a = lcur < 64 ? (lo64 & (~0ull << lcur)) : 0ull;
+    const unsigned long long b = lcur < 64 ? hi64 : (hi64 & (~0ull << (lcur - 64)));
+    Ls = a ? (__ffsll((long long)a) - 1) : (b ? (63 + __ffsll((long long)b)) : 1 << 20);
+  } else {
+    const unsigned long long a = lcur >= 64 ? lo64 : (lo64 & ((2ull << lcur) - 1ull));
+    const unsigned long long b = lcur >= 64 ? (hi64 & ((2ull << (lcur - 64)) - 1ull)) : 0ull;
+    Ls = b ? (127 - __clzll((long long)b)) : (a ? (63 - __clzll((long long)a)) : -(1 << 20));
+  }
+  if (Ls == lcur) return false;
+  const bool reach = up ? (Ls <= lend) : (Ls >= lend);
+  int zlo, zhi;
+  if (up) {
+    zlo = lcur << LS;
+    zhi = (reach ? Ls : lend + 1) << LS;
+  } else {
+    zlo = (reach ? Ls + 1 : lend) << LS;
+    zhi = (lcur + 1) << LS;
+  }
+  if (reach) {
+    const int zb = up ? zlo + (zhi - zlo) : zlo;  // boundary plane of layer Ls facing the ray
+    const float tz = ((float)(zb - w.Oi[2]) - w.Of[2]) * w.invD[2];
+    if (tz < te) {
+      te = tz;
+      ax = 2;
+    }
+  }
+  lo[0] = bx;
+  hi[0] = bx + F;
+  lo[1] = by;
+  hi[1] = by + F;
+  lo[2] = zlo;
+  hi[2] = zhi;
+  *axis = ax;
+  *t_exit = te;
+  return te > w.t;
+}
+
 struct Hit {
   int vox;
   int base[3];
@@ -262,70 +329,95 @@ struct Hit {
   float tin, tout;
 };
 
-// Advance `w` to the next voxel crossed with positive length.  Empty leaves
-// are skipped whole: the ray leaves a leaf box through the face of the
-// nearest exit plane, and the neighbour cell across that face is the next
-// point to locate (other coordinates from the exit point, kept inside the
-// face and never moved backwards, so every hop makes progress).
-__device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h) {
-  while (w.alive) {
+// Leave the box [lo, hi) through its face on `axis` at distance te: the next
+// point to locate is the neighbour cell across that face, the other
+// coordinates taken from the exit point, kept inside the box's face and never
+// moved backwards (so every hop makes progress).
+__device__ __forceinline__ void hop(const DevScene& S, Walk& w, const int lo[3], const int hi[3],
+                                    int axis, float te) {
+  if (!(te < w.tend) || ++w.steps > S.Gf[0] + S.Gf[1] + S.Gf[2] + 64) {
+    if (w.steps > S.Gf[0] + S.Gf[1] + S.Gf[2] + 64) atomicOr(S.status, SALF_DEVERR_STEP_CAP);
+    w.alive = false;
+    return;
+  }
+  bool out = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a == axis) {
+      const int n = w.D[a] > 0.f ? hi[a] : lo[a] - 1;
+      out = n < 0 || n >= S.Gf[a];
+      w.c[a] = n;
+    } else {
+      int q = w.Oi[a] + __float2int_rd(fmaf(te, w.D[a], w.Of[a]));
+      q = min(max(q, lo[a]), hi[a] - 1);
+      q = min(max(q, 0), S.Gf[a] - 1);
+      w.c[a] = w.D[a] > 0.f ? max(q, w.c[a]) : min(q, w.c[a]);
+    }
+  }
+  if (out) w.alive = false;
+  w.t = fmaxf(w.t, te);
+}
+
+// Advance `w` toward the next voxel crossed with positive length, taking at
+// most `budget` structure steps (the caller's warp composites the lanes that
+// found one, then calls again: a small budget keeps lanes of different rays in
+// step, so a warp costs about its heaviest ray, not the sum of per-round
+// maxima).  Empty space is left through the farther of two empty boxes around
+// the current cell: the largest empty aligned pyramid cell, and the column-
+// pyramid skip.
+__device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int budget) {
+  for (int it = 0; it < budget && w.alive; ++it) {
     int ls;
-    int vox = find_leaf(S, w.c[0], w.c[1], w.c[2], &ls);
+    const int vox = find_leaf(S, w.c[0], w.c[1], w.c[2], &ls);
     const int E = 1 << ls;
-    int b[3];
+    int lo[3], hi[3];
     float tx[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      b[a] = w.c[a] & ~(E - 1);
-      int p = (w.D[a] > 0.f ? b[a] + E : b[a]) - w.Oi[a];
+      lo[a] = w.c[a] & ~(E - 1);
+      hi[a] = lo[a] + E;
+      const int p = (w.D[a] > 0.f ? hi[a] : lo[a]) - w.Oi[a];
       tx[a] = ((float)p - w.Of[a]) * w.invD[a];
     }
     int ax = (tx[0] <= tx[1] && tx[0] <= tx[2]) ? 0 : (tx[1] <= tx[2] ? 1 : 2);
     float te = tx[ax];
-    bool found = false;
     if (vox >= 0) {
       float tin = w.t;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        int p = (w.D[a] > 0.f ? b[a] : b[a] + E) - w.Oi[a];
+        const int p = (w.D[a] > 0.f ? lo[a] : hi[a]) - w.Oi[a];
         tin = fmaxf(tin, ((float)p - w.Of[a]) * w.invD[a]);
       }
-      float tout = fminf(te, w.tend);
-      if (tout > tin) {
+      const float tout = fminf(te, w.tend);
+      const bool found = tout > tin;
+      if (found) {
         h.vox = vox;
         h.ls = ls;
-        h.base[0] = b[0];
-        h.base[1] = b[1];
-        h.base[2] = b[2];
+        h.base[0] = lo[0];
+        h.base[1] = lo[1];
+        h.base[2] = lo[2];
         h.tin = tin;
         h.tout = tout;
-        found = true;
       }
+      hop(S, w, lo, hi, ax, te);
+      if (found) return true;
+      continue;
     }
-    // hop to the neighbour across the exit face
-    if (!(te < w.tend) || ++w.steps > w.max_steps) {
-      if (w.steps > w.max_steps) atomicOr(S.status, SALF_DEVERR_STEP_CAP);
-      w.alive = false;
+    // empty: try the column pyramid (current level, then one finer)
+    int clo[3], chi[3], cax;
+    float cte;
+    int cl = w.cl;
+    bool ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
+    if (!ok && cl > 0) {
+      --cl;
+      ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
+    }
+    w.cl = ok ? min(cl + 1, S.CL - 1) : cl;
+    if (ok && cte > te) {
+      hop(S, w, clo, chi, cax, cte);
     } else {
-      int nc[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (a == ax) {
-          nc[a] = w.D[a] > 0.f ? b[a] + E : b[a] - 1;
-        } else {
-          int q = w.Oi[a] + __float2int_rd(fmaf(te, w.D[a], w.Of[a]));
-          q = min(max(q, b[a]), b[a] + E - 1);
-          q = min(max(q, 0), S.Gf[a] - 1);
-          nc[a] = w.D[a] > 0.f ? max(q, w.c[a]) : min(q, w.c[a]);
-        }
-      }
-      if (nc[ax] < 0 || nc[ax] >= S.Gf[ax]) w.alive = false;
-      w.c[0] = nc[0];
-      w.c[1] = nc[1];
-      w.c[2] = nc[2];
-      w.t = fmaxf(w.t, te);
+      hop(S, w, lo, hi, ax, te);
     }
-    if (found) return true;
   }
   return false;
 }
