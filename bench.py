@@ -77,6 +77,22 @@ def driving_fisheye():
     return synth.fisheye(1920, 1080, 190.0, synth.camera_pose_looking((0.0, 0.0, 1.7), 0.0))
 
 
+WORKLOADS = {
+    "camera": dict(sensor=driving_camera, b_field=B_FIELD_EXP_F32, b_out=B_OUT_CAMERA,
+                   want_intensity=False, outputs=("rgb", "depth", "opacity"), metric=METRIC,
+                   workload=WORKLOAD),
+    "lidar": dict(sensor=driving_lidar, b_field=B_FIELD_EXP_INT_F32, b_out=B_OUT_LIDAR,
+                  want_intensity=True, outputs=("depth", "opacity", "intensity"),
+                  metric="Mrays/s, 128x2048 spinning LiDAR, 2M-voxel driving scene (FP32, forward)",
+                  workload="spinning LiDAR 128 beams x 2048 azimuths, elevation -25..+15 deg, "
+                           "per-ray pose, range + intensity, driving scene 2,000,000 voxels (seed 2)"),
+    "fisheye": dict(sensor=driving_fisheye, b_field=B_FIELD_EXP_F32, b_out=B_OUT_CAMERA,
+                    want_intensity=False, outputs=("rgb", "depth", "opacity"),
+                    metric="Mrays/s (valid rays), 1080p 190-degree fisheye, 2M-voxel driving scene",
+                    workload="equidistant fisheye 1920x1080 190deg, driving scene 2,000,000 voxels"),
+}
+
+
 # --------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -354,6 +370,8 @@ def main():
     ap.add_argument("--impl", default="salf", choices=["salf", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--workload", default="camera", choices=["camera", "lidar", "fisheye"],
+                    help="sensor of the headline line (default: the 1080p camera)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -378,11 +396,13 @@ def main():
     sc = synth.driving_scene(2_000_000, seed=2)
     g = P.Scene(sc, dtype="f32", ctx=ctx)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 2x L2
-    cam = driving_camera()
+    wl = WORKLOADS[args.workload]
+    cam = wl["sensor"]()
+    want_int = wl["want_intensity"]
+    outs = wl["outputs"]
     R = cam["width"] * cam["height"]
-    out = {k: torch.empty((R, 3) if k == "rgb" else (R,), device="cuda")
-           for k in ("rgb", "depth", "opacity")}
-    fn = lambda: g.render(cam, out=out, valid=False)
+    out = {k: torch.empty((R, 3) if k == "rgb" else (R,), device="cuda") for k in outs}
+    fn = lambda: g.render(cam, out=out, outputs=outs, valid=False, want_intensity=want_int)
 
     sampler = ClockSampler(gpu_id_for(torch, local))
     for _ in range(args.warmup):
@@ -406,45 +426,50 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
     avg = tot_ms / args.steps
-    value = world * R * args.steps / (tot_ms * 1e-3) / 1e6
+    n_counted = R
+    if args.workload == "fisheye":
+        n_counted = int(g.render(cam, outputs=("opacity",))["valid"].sum().item())
+    value = world * n_counted * args.steps / (tot_ms * 1e-3) / 1e6
 
-    nvis, _ = visits_of(torch, g, cam)
-    bytes_alg = nvis * B_FIELD_EXP_F32 + R * B_OUT_CAMERA
+    nvis, _ = visits_of(torch, g, cam, want_int)
+    bytes_alg = nvis * wl["b_field"] + R * wl["b_out"]
     peak, peak_kind = hbm_peak()
     achieved = bytes_alg / (avg * 1e-3) / 1e9
     traffic = None
     try:
         tj = json.load(open(TRAFFIC_FILE))
         if tj.get("kernel_hash") == kernel_hash():
-            traffic = tj.get("dram_bytes_per_launch")
+            traffic = tj.get("dram_bytes_per_launch", {}).get(args.workload)
     except Exception:
         pass
 
     # end to end through the C ABI with host output buffers (pinned)
     host = {k: torch.empty((R, 3) if k == "rgb" else (R,), dtype=torch.float32, pin_memory=True)
-            for k in ("rgb", "depth", "opacity")}
+            for k in outs}
     for _ in range(args.warmup):
-        g.render_host(cam, out=host)
+        g.render_host(cam, out=host, want_intensity=want_int)
     e2e_steps = max(10, args.steps // 4)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        g.render_host(cam, out=host)
+        g.render_host(cam, out=host, want_intensity=want_int)
     e2e_s = time.perf_counter() - t0
-    e2e_value = world * R * e2e_steps / e2e_s / 1e6
+    e2e_value = world * n_counted * e2e_steps / e2e_s / 1e6
 
-    line = dict(metric=METRIC, value=value, unit="Mrays/s", n_gpus=world, steps=args.steps,
+    line = dict(metric=wl["metric"], value=value, unit="Mrays/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=avg, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(workload=WORKLOAD, l2="flushed between timed steps (256 MiB write)",
+                config=dict(workload=wl["workload"], l2="flushed between timed steps (256 MiB write)",
                             parallelism=f"replicas x{world}", fps=1e3 / avg,
                             visits_per_ray=nvis / R, t_min=1e-4),
                 roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s",
                               frac=achieved / peak, traffic=traffic,
                               peak_source=f"{peak_kind} hbm_gbs",
                               bytes_per_launch=bytes_alg,
-                              kernel="k_forward<F32,EXP>"),
+                              kernel="k_forward<F32,EXP>",
+                              note="bytes = visits x record scalars read + outputs per ray; "
+                                   "visits counted by the kernel"),
                 e2e=dict(value=e2e_value, unit="Mrays/s", h2d_bytes_per_step=0,
-                         d2h_bytes_per_step=R * 20,
+                         d2h_bytes_per_step=R * 4 * (len(outs) + 2 * ("rgb" in outs)),
                          how="salf_render_rays with pinned host output buffers, synchronous"),
                 gpu_launches=args.steps, clocks=clocks)
 

@@ -275,7 +275,11 @@ salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* s,
   for (int k = 0; k < 3; ++k) r->bg[k] = o->background[k];
   r->want_int = o->want_intensity ? 1 : 0;
   r->vcap = o->visits_cap;
-  if (s->kind == SALF_RAYS_EXPLICIT || s->height == 1) {
+#ifndef SALF_LIDAR_ROW_TILES
+#define SALF_LIDAR_ROW_TILES 0
+#endif
+  if (s->kind == SALF_RAYS_EXPLICIT || s->height == 1 ||
+      (SALF_LIDAR_ROW_TILES && s->kind == SALF_LIDAR_SPIN)) {
     r->tile_w = 32;
     r->tile_h = 1;
   } else {

@@ -12,16 +12,22 @@
 // has a hit (ballot).  Lanes whose ray terminated early idle in the ballot.
 #include "traverse.cuh"
 
-// Resident 256-thread blocks per SM the forward kernel is compiled for
-// (bounds its registers per thread).
-#ifndef SALF_FWD_MIN_BLOCKS
-#define SALF_FWD_MIN_BLOCKS 2
+// Resident 256-thread blocks per SM each forward variant is compiled for (it
+// bounds the registers per thread).  Coherent camera batches are throughput-
+// bound and gain from the third block; divergent sensors (fisheye, panorama,
+// LiDAR) are bound by their heaviest warps' latency and lose more to the
+// register spills that the third block costs.
+#ifndef SALF_FWD_BLOCKS_COHERENT
+#define SALF_FWD_BLOCKS_COHERENT 3
+#endif
+#ifndef SALF_FWD_BLOCKS_DIVERGENT
+#define SALF_FWD_BLOCKS_DIVERGENT 2
 #endif
 
 using namespace salf;
 
-template <int DT, int MODE, bool DUMP>
-__global__ void __launch_bounds__(256, SALF_FWD_MIN_BLOCKS) k_forward(const __grid_constant__ LaunchParams P) {
+template <int DT, int MODE, bool DUMP, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_forward(const __grid_constant__ LaunchParams P) {
   const int warp = blockIdx.x * SALF_WARPS_PER_BLOCK + (threadIdx.x >> 5);
   if (warp >= P.total_tiles) return;
   const int lane = threadIdx.x & 31;
@@ -111,22 +117,32 @@ __global__ void __launch_bounds__(256, SALF_FWD_MIN_BLOCKS) k_forward(const __gr
 }
 
 template <int DT, int MODE>
-static cudaError_t launch_fm(const LaunchParams& P, bool dump, cudaStream_t st) {
+static cudaError_t launch_fm(const LaunchParams& P, bool dump, bool coherent, cudaStream_t st) {
   const int blocks = (P.total_tiles + SALF_WARPS_PER_BLOCK - 1) / SALF_WARPS_PER_BLOCK;
   if (blocks == 0) return cudaSuccess;
+  const dim3 g(blocks), b(32 * SALF_WARPS_PER_BLOCK);
   if (dump)
-    k_forward<DT, MODE, true><<<blocks, 32 * SALF_WARPS_PER_BLOCK, 0, st>>>(P);
+    k_forward<DT, MODE, true, SALF_FWD_BLOCKS_DIVERGENT><<<g, b, 0, st>>>(P);
+  else if (coherent)
+    k_forward<DT, MODE, false, SALF_FWD_BLOCKS_COHERENT><<<g, b, 0, st>>>(P);
   else
-    k_forward<DT, MODE, false><<<blocks, 32 * SALF_WARPS_PER_BLOCK, 0, st>>>(P);
+    k_forward<DT, MODE, false, SALF_FWD_BLOCKS_DIVERGENT><<<g, b, 0, st>>>(P);
   return cudaGetLastError();
 }
 
 cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
-  bool dump = false;
-  for (int i = 0; i < P.n_req; ++i) dump = dump || P.req[i].vcap > 0 || P.req[i].ray_dump || P.req[i].steps_out;
+  bool dump = false, coherent = true;
+  for (int i = 0; i < P.n_req; ++i) {
+    const ReqDev& q = P.req[i];
+    dump = dump || q.vcap > 0 || q.ray_dump || q.steps_out;
+    coherent = coherent && (q.kind == SALF_PINHOLE || q.kind == SALF_RAYS_EXPLICIT);
+  }
   const int dt = P.S.dtype, md = P.S.mode;
-  if (dt == SALF_F32 && md == SALF_FIELD_EXP) return launch_fm<SALF_F32, SALF_FIELD_EXP>(P, dump, st);
-  if (dt == SALF_F32 && md == SALF_FIELD_SDF) return launch_fm<SALF_F32, SALF_FIELD_SDF>(P, dump, st);
-  if (dt == SALF_BF16 && md == SALF_FIELD_EXP) return launch_fm<SALF_BF16, SALF_FIELD_EXP>(P, dump, st);
-  return launch_fm<SALF_BF16, SALF_FIELD_SDF>(P, dump, st);
+  if (dt == SALF_F32 && md == SALF_FIELD_EXP)
+    return launch_fm<SALF_F32, SALF_FIELD_EXP>(P, dump, coherent, st);
+  if (dt == SALF_F32 && md == SALF_FIELD_SDF)
+    return launch_fm<SALF_F32, SALF_FIELD_SDF>(P, dump, coherent, st);
+  if (dt == SALF_BF16 && md == SALF_FIELD_EXP)
+    return launch_fm<SALF_BF16, SALF_FIELD_EXP>(P, dump, coherent, st);
+  return launch_fm<SALF_BF16, SALF_FIELD_SDF>(P, dump, coherent, st);
 }

@@ -9,6 +9,14 @@
 
 #include "salf_internal.h"
 
+// Traversal tuning switches (compile-time).
+#ifndef SALF_COL_TRIES
+#define SALF_COL_TRIES 1  // column-pyramid levels tried per empty step
+#endif
+#ifndef SALF_COL_MAX_LS
+#define SALF_COL_MAX_LS 0  // > 0: try the column skip only below this pyramid leaf size
+#endif
+
 namespace salf {
 
 constexpr float kPi = 3.14159265358979323846f;
@@ -407,12 +415,20 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
     int clo[3], chi[3], cax;
     float cte;
     int cl = w.cl;
-    bool ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
-    if (!ok && cl > 0) {
-      --cl;
+    bool ok = false;
+#if SALF_COL_MAX_LS > 0
+    if (ls <= SALF_COL_MAX_LS + S.K)
+#endif
+    {
       ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
+#if SALF_COL_TRIES > 1
+      if (!ok && cl > 0) {
+        --cl;
+        ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
+      }
+#endif
+      w.cl = ok ? min(cl + 1, S.CL - 1) : max(cl - 1, 0);
     }
-    w.cl = ok ? min(cl + 1, S.CL - 1) : cl;
     if (ok && cte > te) {
       hop(S, w, clo, chi, cax, cte);
     } else {
