@@ -305,6 +305,37 @@ def bench_serving(torch, P, duration_s=5.0, seed=6):
         torch.cuda.synchronize()
         lat.append((time.perf_counter() - t0 - at) * 1e3)
     t_seq = time.perf_counter() - t0
+    # saturation: the same requests offered all at once (closed loop)
+    sat = reqs[:min(len(reqs), 400)]
+    sat_rays = sum(s["width"] * s["height"] for _, s in sat)
+    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=2)
+    q2: "queue.Queue" = queue.Queue()
+
+    def consumer2():
+        while True:
+            t = q2.get()
+            if t is None:
+                return
+            srv.poll(t, -1)
+            srv.release(t)
+
+    th = threading.Thread(target=consumer2)
+    th.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _, s in sat:
+        q2.put(srv.submit(s, want_intensity=s["kind"] == "lidar"))
+    q2.put(None)
+    th.join()
+    t_sat_b = time.perf_counter() - t0
+    st_sat = srv.stats()
+    srv.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _, s in sat:
+        g.render(s, want_intensity=s["kind"] == "lidar")
+        torch.cuda.synchronize()
+    t_sat_s = time.perf_counter() - t0
     lat.sort()
     q = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
     return dict(workload=f"20 sensors at 10 Hz Poisson for {duration_s:.0f} s, driving scene "
@@ -313,7 +344,14 @@ def bench_serving(torch, P, duration_s=5.0, seed=6):
                 batched=dict(p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], launches=st["launches"],
                              mrays_s=total_rays / t_end / 1e6, wall_s=t_end),
                 sequential=dict(p50_ms=q(0.5), p99_ms=q(0.99), mrays_s=total_rays / t_seq / 1e6,
-                                wall_s=t_seq))
+                                wall_s=t_seq),
+                saturated=dict(requests=len(sat), rays=sat_rays,
+                               batched_mrays_s=sat_rays / t_sat_b / 1e6,
+                               batched_launches=st_sat["launches"],
+                               sequential_mrays_s=sat_rays / t_sat_s / 1e6,
+                               note="all requests offered at once; sequential = one "
+                                    "salf_render_rays per request in arrival order, "
+                                    "waiting for each"))
 
 
 # --------------------------------------------------------------------- oracle
