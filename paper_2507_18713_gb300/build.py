@@ -38,11 +38,12 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def _compile(src: str, verbose_ptxas: bool, out_dir: str = OUT_DIR, defines=()) -> str:
+def _compile(src: str, verbose_ptxas: bool, out_dir: str = OUT_DIR, defines=(),
+             csrc: str = CSRC) -> str:
     obj = os.path.join(out_dir, os.path.basename(src) + ".o")
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-           "-I", INCLUDE, "-I", CSRC, *[f"-D{d}" for d in defines], "-c",
-           os.path.join(CSRC, src), "-o", obj]
+           "-I", INCLUDE, "-I", csrc, *[f"-D{d}" for d in defines], "-c",
+           os.path.join(csrc, src), "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["-x", "cu"]
         if verbose_ptxas:
@@ -58,15 +59,16 @@ def _compile(src: str, verbose_ptxas: bool, out_dir: str = OUT_DIR, defines=()) 
 
 
 def build(force: bool = False, verbose_ptxas: bool = False, out_dir: str = OUT_DIR,
-          defines=()) -> str:
+          defines=(), csrc: str = CSRC) -> str:
     """Compile every translation unit (in parallel) and link libsalf.so into
-    out_dir (default: the package's _build/), with optional -D defines."""
+    out_dir (default: the package's _build/), with optional -D defines and an
+    alternative source directory."""
     os.makedirs(out_dir, exist_ok=True)
     lib = os.path.join(out_dir, "libsalf.so")
     if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
         return lib
     with cf.ThreadPoolExecutor(max_workers=len(CUDA_SOURCES) + len(CXX_SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas, out_dir, defines),
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas, out_dir, defines, csrc),
                            CUDA_SOURCES + CXX_SOURCES))
     tmp = lib + f".tmp{os.getpid()}"
     cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"]

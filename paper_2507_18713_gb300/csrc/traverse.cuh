@@ -9,10 +9,7 @@
 
 #include "salf_internal.h"
 
-// Traversal tuning switches (compile-time).
-#ifndef SALF_COL_TRIES
-#define SALF_COL_TRIES 1  // column-pyramid levels tried per empty step
-#endif
+// Traversal tuning switch (compile-time).
 #ifndef SALF_COL_MAX_LS
 #define SALF_COL_MAX_LS 0  // > 0: try the column skip only below this pyramid leaf size
 #endif
@@ -389,6 +386,7 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
     }
     int ax = (tx[0] <= tx[1] && tx[0] <= tx[2]) ? 0 : (tx[1] <= tx[2] ? 1 : 2);
     float te = tx[ax];
+    bool found = false;
     if (vox >= 0) {
       float tin = w.t;
 #pragma unroll
@@ -397,43 +395,40 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
         tin = fmaxf(tin, ((float)p - w.Of[a]) * w.invD[a]);
       }
       const float tout = fminf(te, w.tend);
-      const bool found = tout > tin;
-      if (found) {
-        h.vox = vox;
-        h.ls = ls;
-        h.base[0] = lo[0];
-        h.base[1] = lo[1];
-        h.base[2] = lo[2];
-        h.tin = tin;
-        h.tout = tout;
-      }
-      hop(S, w, lo, hi, ax, te);
-      if (found) return true;
-      continue;
-    }
-    // empty: try the column pyramid (current level, then one finer)
-    int clo[3], chi[3], cax;
-    float cte;
-    int cl = w.cl;
-    bool ok = false;
-#if SALF_COL_MAX_LS > 0
-    if (ls <= SALF_COL_MAX_LS + S.K)
-#endif
-    {
-      ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
-#if SALF_COL_TRIES > 1
-      if (!ok && cl > 0) {
-        --cl;
-        ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
-      }
-#endif
-      w.cl = ok ? min(cl + 1, S.CL - 1) : max(cl - 1, 0);
-    }
-    if (ok && cte > te) {
-      hop(S, w, clo, chi, cax, cte);
+      found = tout > tin;
+      h.vox = vox;
+      h.ls = ls;
+      h.base[0] = lo[0];
+      h.base[1] = lo[1];
+      h.base[2] = lo[2];
+      h.tin = tin;
+      h.tout = tout;
     } else {
-      hop(S, w, lo, hi, ax, te);
+      // empty: the column-pyramid skip replaces the pyramid cell if it goes further
+      int clo[3], chi[3], cax;
+      float cte;
+      const int cl = w.cl;
+      bool ok = false;
+#if SALF_COL_MAX_LS > 0
+      if (ls <= SALF_COL_MAX_LS + S.K)
+#endif
+      {
+        ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
+        w.cl = ok ? min(cl + 1, S.CL - 1) : max(cl - 1, 0);
+      }
+      if (ok && cte > te) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = clo[a];
+          hi[a] = chi[a];
+        }
+        ax = cax;
+        te = cte;
+      }
     }
+    // one hop for every lane, whichever box it leaves (keeps the warp converged)
+    hop(S, w, lo, hi, ax, te);
+    if (found) return true;
   }
   return false;
 }
