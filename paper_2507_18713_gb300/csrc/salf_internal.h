@@ -60,6 +60,7 @@ struct DevScene {
   int K;
   int M;
   int Gf[3];
+  int bmin[3], bmax[3];  // tight box of all voxels, finest cells [bmin, bmax)
   int mode, dtype;
   int n;
 };

@@ -329,6 +329,21 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
     D.Gf[a] = d->dims[a] << K;
   }
   D.inv_sfin = 1.0 / s->sfin;
+  // tight box of the occupied voxels: rays are clipped to it (no hit outside)
+  for (int a = 0; a < 3; ++a) {
+    D.bmin[a] = D.Gf[a];
+    D.bmax[a] = 0;
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    const int l = d->level[v];
+    for (int a = 0; a < 3; ++a) {
+      const int lo = d->ijk[3 * v + a] << (K - l);
+      D.bmin[a] = std::min(D.bmin[a], lo);
+      D.bmax[a] = std::max(D.bmax[a], lo + (1 << (K - l)));
+    }
+  }
+  if (n == 0)
+    for (int a = 0; a < 3; ++a) D.bmin[a] = D.bmax[a] = 0;
   D.K = K;
   D.M = M;
   D.mode = d->mode;

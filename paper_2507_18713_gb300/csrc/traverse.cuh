@@ -189,8 +189,9 @@ __device__ __forceinline__ void walk_init(const DevScene& S, const Ray& r, Walk&
     if (fabsf(D) < 1e-20f) D = 1e-20f;
     w.D[a] = D;
     w.invD[a] = 1.f / D;
-    float lo = ((float)(0 - r.Oi[a]) - r.Of[a]) * w.invD[a];
-    float hi = ((float)(S.Gf[a] - r.Oi[a]) - r.Of[a]) * w.invD[a];
+    // clip to the tight box of the voxels (no hit can lie outside it)
+    float lo = ((float)(S.bmin[a] - r.Oi[a]) - r.Of[a]) * w.invD[a];
+    float hi = ((float)(S.bmax[a] - r.Oi[a]) - r.Of[a]) * w.invD[a];
     t0 = fmaxf(t0, fminf(lo, hi));
     t1 = fminf(t1, fmaxf(lo, hi));
   }
@@ -202,7 +203,7 @@ __device__ __forceinline__ void walk_init(const DevScene& S, const Ray& r, Walk&
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     int q = r.Oi[a] + __float2int_rd(fmaf(t0, w.D[a], r.Of[a]));
-    w.c[a] = min(max(q, 0), S.Gf[a] - 1);
+    w.c[a] = min(max(q, S.bmin[a]), max(S.bmax[a] - 1, S.bmin[a]));
   }
 }
 
