@@ -12,13 +12,19 @@
 // has a hit (ballot).  Lanes whose ray terminated early idle in the ballot.
 #include "traverse.cuh"
 
-// Resident 256-thread blocks per SM each forward variant is compiled for (it
-// bounds the registers per thread).  Coherent camera batches are throughput-
-// bound and gain from the third block; divergent sensors (fisheye, panorama,
-// LiDAR) are bound by their heaviest warps' latency and lose more to the
-// register spills that the third block costs.
+// Warps per block and resident blocks per SM of each forward variant (they
+// bound the registers per thread).  Coherent camera batches are throughput-
+// bound and gain from more resident warps; divergent sensors (fisheye,
+// panorama, LiDAR) are bound by their heaviest warps' latency and lose more to
+// the register spills that extra residency costs.
+#ifndef SALF_FWD_WPB_COHERENT
+#define SALF_FWD_WPB_COHERENT 4
+#endif
 #ifndef SALF_FWD_BLOCKS_COHERENT
-#define SALF_FWD_BLOCKS_COHERENT 3
+#define SALF_FWD_BLOCKS_COHERENT 6
+#endif
+#ifndef SALF_FWD_WPB_DIVERGENT
+#define SALF_FWD_WPB_DIVERGENT 8
 #endif
 #ifndef SALF_FWD_BLOCKS_DIVERGENT
 #define SALF_FWD_BLOCKS_DIVERGENT 2
@@ -26,9 +32,9 @@
 
 using namespace salf;
 
-template <int DT, int MODE, bool DUMP, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_forward(const __grid_constant__ LaunchParams P) {
-  const int warp = blockIdx.x * SALF_WARPS_PER_BLOCK + (threadIdx.x >> 5);
+template <int DT, int MODE, bool DUMP, int WPB, int MINB>
+__global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constant__ LaunchParams P) {
+  const int warp = blockIdx.x * WPB + (threadIdx.x >> 5);
   if (warp >= P.total_tiles) return;
   const int lane = threadIdx.x & 31;
   const ReqDev& Q = P.req[find_request(P, warp)];
@@ -116,17 +122,20 @@ __global__ void __launch_bounds__(256, MINB) k_forward(const __grid_constant__ L
   }
 }
 
+template <int DT, int MODE, bool DUMP, int WPB, int MINB>
+static void launch_one(const LaunchParams& P, cudaStream_t st) {
+  const int blocks = (P.total_tiles + WPB - 1) / WPB;
+  if (blocks > 0) k_forward<DT, MODE, DUMP, WPB, MINB><<<blocks, 32 * WPB, 0, st>>>(P);
+}
+
 template <int DT, int MODE>
 static cudaError_t launch_fm(const LaunchParams& P, bool dump, bool coherent, cudaStream_t st) {
-  const int blocks = (P.total_tiles + SALF_WARPS_PER_BLOCK - 1) / SALF_WARPS_PER_BLOCK;
-  if (blocks == 0) return cudaSuccess;
-  const dim3 g(blocks), b(32 * SALF_WARPS_PER_BLOCK);
   if (dump)
-    k_forward<DT, MODE, true, SALF_FWD_BLOCKS_DIVERGENT><<<g, b, 0, st>>>(P);
+    launch_one<DT, MODE, true, SALF_FWD_WPB_DIVERGENT, SALF_FWD_BLOCKS_DIVERGENT>(P, st);
   else if (coherent)
-    k_forward<DT, MODE, false, SALF_FWD_BLOCKS_COHERENT><<<g, b, 0, st>>>(P);
+    launch_one<DT, MODE, false, SALF_FWD_WPB_COHERENT, SALF_FWD_BLOCKS_COHERENT>(P, st);
   else
-    k_forward<DT, MODE, false, SALF_FWD_BLOCKS_DIVERGENT><<<g, b, 0, st>>>(P);
+    launch_one<DT, MODE, false, SALF_FWD_WPB_DIVERGENT, SALF_FWD_BLOCKS_DIVERGENT>(P, st);
   return cudaGetLastError();
 }
 

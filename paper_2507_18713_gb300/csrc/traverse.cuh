@@ -269,8 +269,15 @@ __device__ __forceinline__ int find_leaf(const DevScene& S, int ix, int iy, int 
 // footprint's side.  Returns false if the current layer is occupied in the
 // footprint (no progress at this level).  Fills the skipped box [lo, hi)
 // (finest cells), its exit axis and exit distance.
-__device__ __forceinline__ bool col_skip(const DevScene& S, const Walk& w, int cl, float* t_exit,
-                                         int lo[3], int hi[3], int* axis) {
+// Column mask of the footprint (at level cl) that holds the current cell.
+__device__ __forceinline__ uint4 col_mask(const DevScene& S, const Walk& w, int cl) {
+  const int sh = S.K + cl;
+  return __ldg(&S.col[cl][(unsigned)(w.c[1] >> sh) * (unsigned)S.cdim[cl][0] +
+                          (unsigned)(w.c[0] >> sh)]);
+}
+
+__device__ __forceinline__ bool col_skip(const DevScene& S, const Walk& w, int cl, const uint4 m,
+                                         float* t_exit, int lo[3], int hi[3], int* axis) {
   const int sh = S.K + cl;
   const int F = 1 << sh;
   const int fx = w.c[0] >> sh, fy = w.c[1] >> sh;
@@ -286,7 +293,6 @@ __device__ __forceinline__ bool col_skip(const DevScene& S, const Walk& w, int c
   const float zf = (float)w.Oi[2] + fmaf(fminf(te, w.tend), w.D[2], w.Of[2]) + (up ? 1e-3f : -1e-3f);
   int lend = __float2int_rd(zf) >> LS;
   lend = min(max(lend, 0), S.n_layers - 1);
-  const uint4 m = __ldg(&S.col[cl][(unsigned)fy * (unsigned)S.cdim[cl][0] + (unsigned)fx]);
   const unsigned long long lo64 = ((unsigned long long)m.y << 32) | m.x;
   const unsigned long long hi64 = ((unsigned long long)m.w << 32) | m.z;
   int Ls;  // nearest occupied layer at or beyond lcur in the direction of travel
@@ -373,6 +379,9 @@ __device__ __forceinline__ void hop(const DevScene& S, Walk& w, const int lo[3],
 // pyramid skip.
 __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int budget) {
   for (int it = 0; it < budget && w.alive; ++it) {
+    // the column mask depends only on the cell: issue its load with the pyramid's
+    const int cl = w.cl;
+    const uint4 cmask = col_mask(S, w, cl);
     int ls;
     const int vox = find_leaf(S, w.c[0], w.c[1], w.c[2], &ls);
     const int E = 1 << ls;
@@ -408,13 +417,12 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
       // empty: the column-pyramid skip replaces the pyramid cell if it goes further
       int clo[3], chi[3], cax;
       float cte;
-      const int cl = w.cl;
       bool ok = false;
 #if SALF_COL_MAX_LS > 0
       if (ls <= SALF_COL_MAX_LS + S.K)
 #endif
       {
-        ok = col_skip(S, w, cl, &cte, clo, chi, &cax);
+        ok = col_skip(S, w, cl, cmask, &cte, clo, chi, &cax);
         w.cl = ok ? min(cl + 1, S.CL - 1) : max(cl - 1, 0);
       }
       if (ok && cte > te) {
