@@ -207,6 +207,10 @@ __device__ __forceinline__ void walk_init(const DevScene& S, const Ray& r, Walk&
   }
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ unsigned morton6(unsigned x, unsigned y, unsigned z) {
   return (x & 1u) | ((y & 1u) << 1) | ((z & 1u) << 2) | ((x & 2u) << 2) | ((y & 2u) << 3) |
          ((z & 2u) << 4);
@@ -406,6 +410,9 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
       }
       const float tout = fminf(te, w.tend);
       found = tout > tin;
+      // start fetching the voxel's record: it is read right after this step
+      prefetch_l1(static_cast<const char*>(S.params) +
+                  (size_t)vox * (S.dtype == SALF_F32 ? 128u : 64u));
       h.vox = vox;
       h.ls = ls;
       h.base[0] = lo[0];
