@@ -197,6 +197,51 @@ int salf_step_budget() {
   return budget;
 }
 
+// Tile row whose centre-column ray is closest to horizontal in the world
+// (launch-order heuristic only: near-horizontal rays are the longest in
+// driving scenes; it never changes a result).
+static int horizon_tile_row(const salf_sensor* s, int tile_h, int tiles_y) {
+  if (s->kind == SALF_RAYS_EXPLICIT || tiles_y <= 1) return 0;
+  int best = 0;
+  double best_z = 2.0;
+  for (int ty = 0; ty < tiles_y; ++ty) {
+    const double v = std::min((double)s->height - 0.5, ty * tile_h + 0.5 * tile_h);
+    double d[3];
+    if (s->kind == SALF_LIDAR_SPIN) {
+      const double e = s->elev_max - (s->height > 1 ? (v - 0.5) * ((double)s->elev_max - s->elev_min) /
+                                                         (s->height - 1) : 0.0);
+      d[0] = std::cos(e);
+      d[1] = 0.0;
+      d[2] = std::sin(e);
+    } else if (s->kind == SALF_PANO_EQUIRECT) {
+      const double lat = s->elev_max - (v / s->height) * ((double)s->elev_max - s->elev_min);
+      d[0] = 0.0;
+      d[1] = -std::sin(lat);
+      d[2] = std::cos(lat);
+    } else {
+      const double my = (v - s->cy) / s->fy;
+      if (s->kind == SALF_FISHEYE_EQUIDIST) {
+        const double th = std::fabs(my);
+        d[0] = 0.0;
+        d[1] = (my < 0 ? -1.0 : 1.0) * std::sin(th);
+        d[2] = std::cos(th);
+      } else {
+        d[0] = 0.0;
+        d[1] = my;
+        d[2] = 1.0;
+      }
+    }
+    const double wz = s->pose0[8] * d[0] + s->pose0[9] * d[1] + s->pose0[10] * d[2];
+    const double nn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double z = std::fabs(wz / nn);
+    if (z < best_z) {
+      best_z = z;
+      best = ty;
+    }
+  }
+  return best;
+}
+
 int64_t salf_request_rays(const salf_sensor* sen) {
   return (int64_t)sen->width * (int64_t)sen->height;
 }
@@ -287,7 +332,9 @@ salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* s,
     r->tile_h = SALF_TILE_H;
   }
   r->tiles_x = (s->width + r->tile_w - 1) / r->tile_w;
-  r->n_tiles = r->tiles_x * ((s->height + r->tile_h - 1) / r->tile_h);
+  r->tiles_y = (s->height + r->tile_h - 1) / r->tile_h;
+  r->n_tiles = r->tiles_x * r->tiles_y;
+  r->first_row = horizon_tile_row(s, r->tile_h, r->tiles_y);
   return SALF_OK;
 }
 

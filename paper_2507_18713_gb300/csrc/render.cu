@@ -39,10 +39,10 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   const int lane = threadIdx.x & 31;
   const ReqDev& Q = P.req[find_request(P, warp)];
   const DevScene& S = P.S;
-  const int tile = warp - Q.tile_begin;
-  const int tx = tile % Q.tiles_x, ty = tile / Q.tiles_x;
-  const int u = tx * Q.tile_w + lane % Q.tile_w;
-  const int v = ty * Q.tile_h + lane / Q.tile_w;
+  int u0, v0;
+  tile_origin(Q, warp - Q.tile_begin, &u0, &v0);
+  const int u = u0 + lane % Q.tile_w;
+  const int v = v0 + lane / Q.tile_w;
   const bool in_img = (u < Q.W) && (v < Q.H);
   const int ray = v * Q.W + u;
 

@@ -95,10 +95,12 @@ struct ReqDev {
   float t_min;
   float bg[3];
   int want_int;
-  // tiling
-  int tiles_x;
+  // tiling: tile rows are launched outward from first_row, alternating below
+  // and above it (the most nearly horizontal rays, the longest ones, first)
+  int tiles_x, tiles_y;
   int tile_w, tile_h;
   int tile_begin, n_tiles;
+  int first_row;
   // backward inputs (unused by the forward kernel)
   const float* bsaved;
   const float* g_rgb;

@@ -556,6 +556,23 @@ __device__ __forceinline__ void sh_basis(const float d[3], float gam[4]) {
   gam[3] = kSH1 * d[0];
 }
 
+// Launch-order tile row k -> tile row: first_row, first_row + 1, first_row - 1,
+// first_row + 2, ... (rows past one edge continue on the other side).
+__device__ __forceinline__ int zigzag_row(int k, int first, int rows) {
+  const int below = rows - 1 - first;  // rows after `first`
+  const int m = min(first, below);     // pairs that alternate
+  if (k <= 2 * m) return (k & 1) ? first + (k + 1) / 2 : first - k / 2;
+  const int rest = k - 2 * m;          // only one side left
+  return below > first ? first + m + rest : first - m - rest;
+}
+
+// Tile of a warp: (pixel column, pixel row) of its first lane.
+__device__ __forceinline__ void tile_origin(const ReqDev& Q, int tile, int* u0, int* v0) {
+  const int tx = tile % Q.tiles_x, k = tile / Q.tiles_x;
+  *u0 = tx * Q.tile_w;
+  *v0 = zigzag_row(k, Q.first_row, Q.tiles_y) * Q.tile_h;
+}
+
 // Warp tile -> request, pixel.
 __device__ __forceinline__ int find_request(const LaunchParams& P, int warp) {
   int r = 0;
