@@ -157,6 +157,24 @@ def gpu_id_for(torch, dev: int) -> str:
         return vis.split(",")[dev] if vis else str(dev)
 
 
+# --------------------------------------------------------------------- replicas
+
+def replica_throughput(local_ms: float, local_units: int, steps: int, dist=None, device="cpu"):
+    """Whole-job throughput of N independent replicas: every rank processed
+    local_units per step for `steps` steps in local_ms; the job took the
+    slowest rank's time.  Returns (units per second, max ms over ranks)."""
+    t = local_ms
+    units = local_units
+    if dist is not None and dist.is_initialized():
+        import torch
+        v = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        u = torch.tensor([local_units], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        t, units = float(v.item()), int(u.item())
+    return units * steps / (t * 1e-3), t
+
+
 # --------------------------------------------------------------------- timing
 
 def timed_renders(torch, fn, steps, warmup, flush):
@@ -458,16 +476,12 @@ def main():
     if dist:
         dist.barrier()
     g.check()
-    tot_ms = sum(ms)
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    avg = tot_ms / args.steps
     n_counted = R
     if args.workload == "fisheye":
         n_counted = int(g.render(cam, outputs=("opacity",))["valid"].sum().item())
-    value = world * n_counted * args.steps / (tot_ms * 1e-3) / 1e6
+    rate, tot_ms = replica_throughput(sum(ms), n_counted, args.steps, dist, "cuda")
+    avg = tot_ms / args.steps
+    value = rate / 1e6
 
     nvis, _ = visits_of(torch, g, cam, want_int)
     bytes_alg = nvis * wl["b_field"] + R * wl["b_out"]

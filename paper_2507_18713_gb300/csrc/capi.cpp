@@ -280,20 +280,23 @@ salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* s,
   r->elev_step = s->height > 1 ? (float)(((double)s->elev_max - (double)s->elev_min) / (s->height - 1)) : 0.f;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) r->R0[3 * i + j] = (float)s->pose0[4 * i + j];
-  double q0[4], q1[4];
-  mat_to_quat(s->pose0, q0);
-  mat_to_quat(s->pose1, q1);
-  double dot = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2] + q0[3] * q1[3];
-  if (dot < 0) {
-    dot = -dot;
-    for (int k = 0; k < 4; ++k) q1[k] = -q1[k];
-  }
-  const double th = std::acos(std::min(1.0, dot));
-  r->theta = (float)th;
-  r->inv_sin_theta = th > 1e-4 ? (float)(1.0 / std::sin(th)) : 0.f;
-  for (int k = 0; k < 4; ++k) {
-    r->q0[k] = (float)q0[k];
-    r->q1[k] = (float)q1[k];
+  // relative rotation R1 R0^T as (world axis, angle), shortest way round: the
+  // slerp geodesic from R0 to R1 is R(s) = rot(axis, s * angle) R0
+  {
+    double Rr[12] = {0};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double acc = 0;
+        for (int k = 0; k < 3; ++k) acc += s->pose1[4 * i + k] * s->pose0[4 * j + k];
+        Rr[4 * i + j] = acc;
+      }
+    double q[4];
+    mat_to_quat(Rr, q);
+    if (q[0] < 0)
+      for (int k = 0; k < 4; ++k) q[k] = -q[k];
+    const double vn = std::sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    r->rel_angle = vn > 0 ? (float)(2.0 * std::atan2(vn, q[0])) : 0.f;
+    for (int k = 0; k < 3; ++k) r->rel_axis[k] = vn > 0 ? (float)(q[k + 1] / vn) : 0.f;
   }
   const bool timed = s->t1 > s->t0;
   r->moving = (s->kind == SALF_LIDAR_SPIN && timed) ||

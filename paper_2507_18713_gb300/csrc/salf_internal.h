@@ -72,8 +72,10 @@ struct ReqDev {
   float inv_fx, inv_fy, cx, cy;
   float half_fov, elev_min, elev_max, elev_step;
   float R0[9];         // rotation at t0
-  float q0[4], q1[4];  // rotations at t0, t1 as unit quaternions (w, x, y, z), same hemisphere
-  float theta, inv_sin_theta;  // slerp angle between q0 and q1 (theta < 1e-4: normalised lerp)
+  // R(t) = rotation by s * rel_angle about rel_axis (world frame) applied
+  // after R0, s = (t - t0) / (t1 - t0): the slerp geodesic from R0 to R1
+  float rel_axis[3];
+  float rel_angle;
   int Oi[3];           // sensor origin at t0 in finest-cell units: Oi + Of
   float Of[3];
   float dO[3];         // origin(t1) - origin(t0), finest-cell units

@@ -29,19 +29,6 @@ struct Ray {
   bool valid;
 };
 
-__device__ __forceinline__ void quat_to_mat(const float q[4], float R[9]) {
-  float w = q[0], x = q[1], y = q[2], z = q[3];
-  R[0] = 1.f - 2.f * (y * y + z * z);
-  R[1] = 2.f * (x * y - w * z);
-  R[2] = 2.f * (x * z + w * y);
-  R[3] = 2.f * (x * y + w * z);
-  R[4] = 1.f - 2.f * (x * x + z * z);
-  R[5] = 2.f * (y * z - w * x);
-  R[6] = 2.f * (x * z - w * y);
-  R[7] = 2.f * (y * z + w * x);
-  R[8] = 1.f - 2.f * (x * x + y * y);
-}
-
 // Sensor ray of pixel (u, v) / LiDAR (azimuth u, beam v).
 __device__ __forceinline__ void gen_ray(const ReqDev& Q, const DevScene& S, int u, int v,
                                         int ray, Ray& r) {
@@ -73,10 +60,10 @@ __device__ __forceinline__ void gen_ray(const ReqDev& Q, const DevScene& S, int 
   float s = 0.f;
   if (Q.kind == SALF_LIDAR_SPIN) {
     float e = Q.elev_max - (float)v * Q.elev_step;
-    float ph = (2.f * kPi) * ((float)u / (float)Q.W);
     float se, ce, sp, cp;
     sincosf(e, &se, &ce);
-    sincosf(ph, &sp, &cp);
+    // azimuth 2 pi u / W as sin/cos(pi x) with x = 2u/W: no rounding of 2 pi
+    sincospif(2.f * (float)u / (float)Q.W, &sp, &cp);
     dc[0] = ce * cp;
     dc[1] = ce * sp;
     dc[2] = se;
@@ -98,10 +85,10 @@ __device__ __forceinline__ void gen_ray(const ReqDev& Q, const DevScene& S, int 
       dc[1] = k * my;
       dc[2] = ct;
     } else {  // equirectangular panorama
-      float lon = (2.f * kPi) * (px / (float)Q.W - 0.5f);
+      // longitude 2 pi (px / W - 0.5) as sin/cos(pi x): no rounding of 2 pi
       float lat = Q.elev_max - (py / (float)Q.H) * (Q.elev_max - Q.elev_min);
       float sl, cl, sa, ca;
-      sincosf(lon, &sl, &cl);
+      sincospif(2.f * px / (float)Q.W - 1.f, &sl, &cl);
       sincosf(lat, &sa, &ca);
       dc[0] = ca * sl;
       dc[1] = -sa;
@@ -109,33 +96,22 @@ __device__ __forceinline__ void gen_ray(const ReqDev& Q, const DevScene& S, int 
     }
     if (Q.moving) s = (float)v / (float)(Q.H - 1);
   }
-  float R[9];
-  if (s > 0.f) {
-    float q[4];
-    if (Q.theta > 1e-4f) {
-      float a = sinf((1.f - s) * Q.theta) * Q.inv_sin_theta;
-      float b = sinf(s * Q.theta) * Q.inv_sin_theta;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) q[k] = a * Q.q0[k] + b * Q.q1[k];
-    } else {
-      float nn = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        q[k] = (1.f - s) * Q.q0[k] + s * Q.q1[k];
-        nn += q[k] * q[k];
-      }
-      float inv = rsqrtf(nn);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) q[k] *= inv;
-    }
-    quat_to_mat(q, R);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = Q.R0[k];
+  float d0 = Q.R0[0] * dc[0] + Q.R0[1] * dc[1] + Q.R0[2] * dc[2];
+  float d1 = Q.R0[3] * dc[0] + Q.R0[4] * dc[1] + Q.R0[5] * dc[2];
+  float d2 = Q.R0[6] * dc[0] + Q.R0[7] * dc[1] + Q.R0[8] * dc[2];
+  if (s > 0.f && Q.rel_angle != 0.f) {
+    // Rodrigues rotation by alpha about k: d + sin(a) (k x d) + (1 - cos(a)) k x (k x d)
+    const float a = s * Q.rel_angle;
+    float sh, ch;
+    sincosf(0.5f * a, &sh, &ch);
+    const float sa = 2.f * sh * ch, omc = 2.f * sh * sh;
+    const float kx = Q.rel_axis[0], ky = Q.rel_axis[1], kz = Q.rel_axis[2];
+    const float cx = ky * d2 - kz * d1, cy = kz * d0 - kx * d2, cz = kx * d1 - ky * d0;
+    const float ccx = ky * cz - kz * cy, ccy = kz * cx - kx * cz, ccz = kx * cy - ky * cx;
+    d0 = fmaf(omc, ccx, fmaf(sa, cx, d0));
+    d1 = fmaf(omc, ccy, fmaf(sa, cy, d1));
+    d2 = fmaf(omc, ccz, fmaf(sa, cz, d2));
   }
-  float d0 = R[0] * dc[0] + R[1] * dc[1] + R[2] * dc[2];
-  float d1 = R[3] * dc[0] + R[4] * dc[1] + R[5] * dc[2];
-  float d2 = R[6] * dc[0] + R[7] * dc[1] + R[8] * dc[2];
   float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
   r.d[0] = d0 * inv;
   r.d[1] = d1 * inv;

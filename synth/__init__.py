@@ -14,6 +14,7 @@ from .scenes import (  # noqa: F401
     tiny_scene,
     driving_scene,
     random_multilevel_scene,
+    deep_scene,
     single_voxel_scene,
     shuffle_scene,
 )

@@ -143,6 +143,37 @@ def random_multilevel_scene(dims=(6, 5, 4), max_level: int = 2, p_occ: float = 0
                      f"multilevel-{seed}")
 
 
+def deep_scene(max_level: int = 10, dims=(2, 2, 2), seed: int = 0, s0: float = 1.0,
+               origin=(0.0, 0.0, 0.0), p_sibling: float = 0.7, mode: str = "exp") -> SceneData:
+    """Voxels at every level down to max_level: in each level-0 cell one
+    random child is subdivided again at every level (a "spine") and each of
+    its 7 siblings is kept as a voxel with probability p_sibling."""
+    rng = np.random.default_rng(seed)
+    levels, cells = [], []
+    for k in range(dims[2]):
+        for j in range(dims[1]):
+            for i in range(dims[0]):
+                c = (i, j, k)
+                for l in range(max_level):
+                    go = int(rng.integers(8))
+                    for o in range(8):
+                        ch = (2 * c[0] + (o & 1), 2 * c[1] + ((o >> 1) & 1), 2 * c[2] + (o >> 2))
+                        if o == go:
+                            nxt = ch
+                        elif rng.random() < p_sibling:
+                            levels.append(l + 1)
+                            cells.append(ch)
+                    c = nxt
+                levels.append(max_level)
+                cells.append(c)
+    n = len(levels)
+    params = draw_params(rng, n, mode, dtype=np.float64)
+    return SceneData(tuple(origin), float(s0), tuple(dims), int(max_level),
+                     np.asarray(levels, dtype=np.uint8),
+                     np.asarray(cells, dtype=np.int32).reshape(-1, 3), params, mode,
+                     f"deep-{max_level}")
+
+
 def shuffle_scene(scene: SceneData, seed: int) -> tuple[SceneData, np.ndarray]:
     """Same voxel set in a random input order; returns (scene, perm) with
     new[i] = old[perm[i]]."""

@@ -116,12 +116,62 @@ def test_bf16_records(salf, oracle_lib):
     q = torch.from_numpy(sc.params.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
     res = _full(salf, oracle_lib, sc, c1_camera(), dtype="bf16", params_for_oracle=q)
     assert res["errs"]["max_c"] <= TOL_C
+    # error of BF16 storage against the FP64 oracle on the FP32 records, per
+    # output (reported, not asserted: it is the storage format's own error)
     osc32 = oracle_lib.OracleScene(sc)
-    o32 = oracle_lib.render(osc32, c1_camera())
+    o32 = oracle_lib.render(osc32, c1_camera(), want_intensity=True)
     g = salf.Scene(sc, dtype="bf16")
-    gb = gpu_render(g, c1_camera())
-    qerr = float(np.abs(gb["rgb"] - o32["rgb"]).max())
-    print(f"BF16 quantisation error vs FP32 records (rgb, abs max): {qerr:.3g}")
+    gb = gpu_render(g, c1_camera(), want_intensity=True,
+                    outputs=("rgb", "depth", "opacity", "intensity"))
+    errs = {k: float(np.abs(gb[k] - o32[k]).max()) for k in ("rgb", "depth", "opacity", "intensity")}
+    print("BF16 storage error vs FP64 oracle on FP32 records (abs max):", errs)
+
+
+def test_deep_octree_all_levels(salf, oracle_lib):
+    """Voxels at every level 0..10 (edge down to 1/1024 of a level-0 cell);
+    rays aimed at the spines' tips cross many tiny voxels."""
+    sc = synth.deep_scene(max_level=10, dims=(2, 2, 2), seed=3)
+    assert set(np.unique(sc.level)) == set(range(1, 11))
+    osc = oracle_lib.OracleScene(sc)
+    assert osc.status == 0
+    tips = [(sc.ijk[v] + 0.5) / (1 << 10) * sc.s0 for v in np.where(sc.level == 10)[0]]
+    rng = np.random.default_rng(0)
+    rays = []
+    for tip in tips:
+        for _ in range(64):
+            o = np.array(tip) + rng.normal(size=3) * 1.5
+            d = np.array(tip) - o + rng.normal(size=3) * 1e-3
+            rays.append(np.concatenate([o, d / np.linalg.norm(d), [0.0, 0.0]]))
+    sen = synth.explicit_rays(np.array(rays))
+    res = _full(salf, oracle_lib, sc, sen, t_min=0.0, brute=True)
+    n, bad = res["visits"]
+    assert bad <= max(3, n // 50), res
+    assert res["mean_visits"] > 3
+    cam = synth.pinhole(96, 72, 80.0, synth.camera_pose_looking((-1.5, 0.9, 1.1), 0.1))
+    res = _full(salf, oracle_lib, sc, cam, brute=True)
+    assert res["visits"][1] <= max(3, res["visits"][0] // 100)
+
+
+def test_size_limits_rejected(salf):
+    r = np.zeros((1, 32), np.float32)
+    too_wide = synth.single_voxel_scene(r, dims=(4097, 1, 1), max_level=10)
+    with pytest.raises(salf.SalfError) as e:
+        salf.Scene(too_wide)            # dims << max_level > 2^21
+    assert e.value.status == 1
+    too_deep = synth.single_voxel_scene(r, max_level=11)
+    with pytest.raises(salf.SalfError) as e:
+        salf.Scene(too_deep)
+    assert e.value.status == 1
+    g = salf.Scene(synth.single_voxel_scene(r))
+    huge = synth.pinhole(65536, 65536, 60.0, synth.camera_pose_looking((-1, 0.5, 0.5), 0.0))
+    with pytest.raises(salf.SalfError) as e:
+        g.render(huge, outputs=("opacity",), valid=False)   # > 2^31 - 1 rays
+    assert e.value.status == 1
+    bad_fx = synth.pinhole(8, 8, 60.0, synth.camera_pose_looking((-1, 0.5, 0.5), 0.0))
+    bad_fx["fx"] = 0.0
+    with pytest.raises(salf.SalfError) as e:
+        g.render(bad_fx)
+    assert e.value.status == 1
 
 
 def test_empty_and_degenerate_scenes(salf, oracle_lib):
@@ -306,7 +356,9 @@ def test_generated_rays_match_oracle(salf, oracle_lib, kind):
         assert np.array_equal(dump[:, 7] > 0, valid)
     d = dump[:, 3:6] / np.linalg.norm(dump[:, 3:6], axis=1, keepdims=True)
     ang = np.linalg.norm(np.cross(d, ref["d"]), axis=1)[valid]
-    lim = 1.5e-7 if kind == "pinhole" else 8e-7
+    lim = 1.5e-7 if kind == "pinhole" else 3e-7
+    print(f"{kind}: max direction error {ang.max():.3g} rad, origin error "
+          f"{np.abs(dump[:, :3] - ref['o']).max():.3g} m")
     assert ang.max() <= lim, (kind, ang.max())
     assert np.abs(dump[:, :3] - ref["o"]).max() <= 2e-6
     assert np.abs(dump[:, 6] - ref["tau"]).max() <= 1e-7 + 1e-6 * abs(sen["t1"])

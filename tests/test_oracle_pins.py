@@ -521,3 +521,20 @@ def test_adjoint_matches_finite_differences(oracle_lib, mode):
     assert np.all(grad[:, 31] == 0)
     if mode == "exp":
         assert np.all(grad[:, 25:27] == 0)
+
+
+def test_dda_candidates_equal_brute_force_deep_octree(oracle_lib):
+    """Voxels at every level 0..10: the finest-level walk (2048 cells per axis)
+    still enumerates exactly the brute-force hit list."""
+    sc = synth.deep_scene(max_level=10, dims=(2, 2, 2), seed=3)
+    osc = oracle_lib.OracleScene(sc)
+    rng = np.random.default_rng(1)
+    tips = [(sc.ijk[v] + 0.5) / 1024.0 for v in np.where(sc.level == 10)[0]]
+    for tip in tips:
+        for _ in range(16):
+            o = np.array(tip) + rng.normal(size=3) * 1.5
+            d = np.array(tip) - o + rng.normal(size=3) * 1e-3
+            d /= np.linalg.norm(d)
+            a = oracle_lib.trace(osc, o, d, brute_force=True)
+            b = oracle_lib.trace(osc, o, d, brute_force=False)
+            assert [h[0] for h in a] == [h[0] for h in b]
