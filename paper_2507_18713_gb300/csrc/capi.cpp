@@ -323,13 +323,13 @@ salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* s,
   for (int k = 0; k < 3; ++k) r->bg[k] = o->background[k];
   r->want_int = o->want_intensity ? 1 : 0;
   r->vcap = o->visits_cap;
-#ifndef SALF_LIDAR_ROW_TILES
-#define SALF_LIDAR_ROW_TILES 0
-#endif
-  if (s->kind == SALF_RAYS_EXPLICIT || s->height == 1 ||
-      (SALF_LIDAR_ROW_TILES && s->kind == SALF_LIDAR_SPIN)) {
+  if (s->kind == SALF_RAYS_EXPLICIT || s->height == 1) {
     r->tile_w = 32;
     r->tile_h = 1;
+  } else if (s->kind == SALF_LIDAR_SPIN) {
+    // 4 azimuths x 8 beams per warp: measured faster than 8 x 4 for spinning LiDARs
+    r->tile_w = 4;
+    r->tile_h = 8;
   } else {
     r->tile_w = SALF_TILE_W;
     r->tile_h = SALF_TILE_H;

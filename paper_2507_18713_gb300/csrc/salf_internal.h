@@ -14,8 +14,10 @@
 #define SALF_MAX_MASK_LEVELS 12
 #define SALF_MAX_COL_LEVELS 16
 #define SALF_MAX_BATCH 24
-#define SALF_TILE_W 8
-#define SALF_TILE_H 4
+#ifndef SALF_TILE_W
+#define SALF_TILE_W 8  // camera warp tile: SALF_TILE_W x (32 / SALF_TILE_W) pixels
+#endif
+#define SALF_TILE_H (32 / SALF_TILE_W)
 #define SALF_WARPS_PER_BLOCK 8
 
 // Device status-word bits.

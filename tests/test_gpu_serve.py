@@ -156,3 +156,45 @@ def test_destroy_with_pending_requests_does_not_hang(salf, scene):
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 30
+
+
+def test_serving_scene_4m_bf16_parity_and_mix_equality(salf, oracle_lib):
+    """The serving configuration at full size: 4,000,000-voxel scene (two ground
+    layers, 600 actors), BF16 records.  Sampled outputs of the serving sensor
+    kinds match the oracle on the dequantised records; each request's result is
+    identical alone and inside a batch."""
+    from tests.parity_util import compare_outputs, oracle_sensitivity
+    sc = synth.driving_scene(4_000_000, seed=3, ground_layers=2, n_actors=600)
+    g = salf.Scene(sc, dtype="bf16")
+    q = torch.from_numpy(sc.params).to(torch.bfloat16).double().numpy()
+    osc = oracle_lib.OracleScene(sc, params=q)
+    sensors = [
+        synth.panorama(4096, 1024, synth.camera_pose_looking((0.3, -0.2, 1.7), 0.4)),
+        synth.fisheye(1280, 960, 190.0, synth.camera_pose_looking((0.1, 0.2, 1.65), 2.0)),
+        synth.lidar(64, 1024, synth.lidar_pose((0.0, 0.1, 1.9), 1.0),
+                    synth.lidar_pose((1.0, 0.1, 1.9), 1.02), t0=0.0, t1=0.1),
+        synth.pinhole(1920, 1080, 60.0, synth.camera_pose_looking((-0.2, 0.3, 1.72), -1.3)),
+    ]
+    srv = salf.Server(g, mem_budget_bytes=1 << 30, n_streams=2)
+    tickets = [srv.submit(s, want_intensity=s["kind"] == "lidar") for s in sensors]
+    for i, (s, t) in enumerate(zip(sensors, tickets)):
+        wi = s["kind"] == "lidar"
+        res = srv.fetch(t, timeout_ms=60000)
+        lone = g.render(s, want_intensity=wi,
+                        outputs=("rgb", "depth", "opacity") + (("intensity",) if wi else ()))
+        torch.cuda.synchronize()
+        for k in ("depth", "opacity", "valid") + (("intensity",) if wi else ("rgb",)):
+            assert torch.equal(res[k], lone[k]), (s["kind"], k)
+        srv.release(t)
+        R = s["width"] * s["height"]
+        idx = synth.sample_ray_indices(R, 8192, 40 + i)
+        gr = {k: v.cpu().numpy()[idx] for k, v in lone.items() if not k.startswith("_")}
+        if "intensity" not in gr:
+            gr["intensity"] = np.zeros(len(idx))
+        orr = oracle_lib.render(osc, s, idx=idx, want_intensity=wi)
+        sens = lambda pos, s=s, idx=idx, wi=wi: oracle_sensitivity(
+            oracle_lib, osc, s, idx[pos], t_min=1e-4, want_intensity=wi)
+        r = compare_outputs(gr, orr, want_intensity=wi, t_min=1e-4, sensitivity=sens)
+        print(s["kind"], r)
+    srv.close()
+    g.check()
