@@ -70,17 +70,14 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ Launch
     const bool hit = next_hit(S, w, h, budget);
     if (!__any_sync(0xffffffffu, hit || w.alive)) break;
     if (hit) {
-      Record<DT> rec;
-      rec.load(S.params, h.vox, want_int);
       const float tm = 0.5f * (h.tin + h.tout);
       const float dl = h.tout - h.tin;
       float x[3];
       local_coords(w, h, tm, x);
-      float lin;
-      const float sig = density<MODE>(rec.v, x, &lin);
-      float c[3];
-      colour(rec.v, x, gam, c);
-      const float io = want_int ? intensity_field(rec.v, x) : 0.f;
+      Field f;
+      field_eval<DT, MODE>(S, h.vox, want_int, x, gam, f);
+      const float sig = f.sig, lin = f.lin, io = f.io;
+      const float* c = f.c;
       const float e = __expf(-sig * dl);
       const float wgt = T * (1.f - e);
       const float gq = g[0] * c[0] + g[1] * c[1] + g[2] * c[2] + g[3] * tm + g[4] + g[5] * io;
@@ -97,7 +94,7 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ Launch
 #pragma unroll
         for (int q = 0; q < 4; ++q) gr[q] = dsig * sig * xh[q];
       } else {
-        const float a = rec.v[25], b = rec.v[26];
+        const float a = f.a, b = f.b;
         const float ex = __expf(-fabsf(lin) / b);
         const float ds = dsig * (a / (2.f * b)) * ex;
 #pragma unroll

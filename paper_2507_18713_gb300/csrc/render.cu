@@ -21,7 +21,7 @@
 #define SALF_FWD_WPB_COHERENT 4
 #endif
 #ifndef SALF_FWD_BLOCKS_COHERENT
-#define SALF_FWD_BLOCKS_COHERENT 6
+#define SALF_FWD_BLOCKS_COHERENT 7
 #endif
 #ifndef SALF_FWD_WPB_DIVERGENT
 #define SALF_FWD_WPB_DIVERGENT 8
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   sh_basis(r.d, gam);
   const bool want_int = Q.want_int != 0;
   const float tmin = Q.t_min;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dp = 0.f, Op = 0.f, Ip = 0.f;
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dp = 0.f, Ip = 0.f;
   int nvis = 0;
 
   const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
@@ -69,24 +69,20 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
     const bool hit = next_hit(S, w, h, budget);
     if (!__any_sync(0xffffffffu, hit || w.alive)) break;
     if (hit) {
-      Record<DT> rec;
-      rec.load(S.params, h.vox, want_int);
       const float tm = 0.5f * (h.tin + h.tout);
       const float dl = h.tout - h.tin;
       float x[3];
       local_coords(w, h, tm, x);
-      float lin;
-      const float sig = density<MODE>(rec.v, x, &lin);
-      float c[3];
-      colour(rec.v, x, gam, c);
-      const float io = want_int ? intensity_field(rec.v, x) : 0.f;
+      Field f;
+      field_eval<DT, MODE>(S, h.vox, want_int, x, gam, f);
+      const float sig = f.sig, io = f.io;
+      const float* c = f.c;
       const float e = __expf(-sig * dl);   // 1 - alpha (Eq. 4)
       const float wgt = T * (1.f - e);     // T_i alpha_i (Eq. 3)
       C0 = fmaf(wgt, c[0], C0);
       C1 = fmaf(wgt, c[1], C1);
       C2 = fmaf(wgt, c[2], C2);
       Dp = fmaf(wgt, tm, Dp);
-      Op += wgt;
       Ip = fmaf(wgt, io, Ip);
       T *= e;
       if (DUMP) {
@@ -98,6 +94,7 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   }
   if (!in_img) return;
   const bool valid = r.valid;
+  const float Op = 1.f - T;  // sum of T_i alpha_i telescopes to 1 - T_end (Eq. 3-4)
   if (Q.rgb) {
     float* o = Q.rgb + 3 * (size_t)ray;
     o[0] = valid ? fmaf(T, Q.bg[0], C0) : 0.f;

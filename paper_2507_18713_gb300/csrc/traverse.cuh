@@ -549,6 +549,69 @@ __device__ __forceinline__ void tile_origin(const ReqDev& Q, int tile, int* u0, 
   *v0 = zigzag_row(k, Q.first_row, Q.tiles_y) * Q.tile_h;
 }
 
+// Local field of one voxel at local coordinates x (Eq. 1 or 5-6, Eq. 2, and
+// the intensity field): density, the affine geometry value, colour,
+// intensity, and the SDF parameters a, b.
+struct Field {
+  float sig, lin, c[3], io, a, b;
+};
+
+__device__ __forceinline__ float sdf_density(float s, float a, float b) {
+  const float e = __expf(-fabsf(s) / b);
+  const float sg = (s > 0.f) ? 1.f : ((s < 0.f) ? -1.f : 0.f);
+  return 0.5f * a + 0.5f * a * sg * (1.f - e);
+}
+
+// FP32 records are read in two stages (a compiler barrier keeps the second
+// stage's loads below the first stage's arithmetic), so only half of the
+// record is live in registers at a time.  Slots: Wsigma 0-3, W_c 4-12 (rows
+// r, g, b), W_sh 13-24 (rows r, g, b), a 25, b 26, W_int 27-30.
+template <int DT, int MODE>
+__device__ __forceinline__ void field_eval(const DevScene& S, int vox, bool want_int,
+                                           const float x[3], const float gam[4], Field& f) {
+  if (DT == SALF_F32) {
+    const float4* p = reinterpret_cast<const float4*>(S.params) + (size_t)vox * 8;
+    const float4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2), q3 = __ldg(p + 3);
+    f.lin = fmaf(q0.x, x[0], fmaf(q0.y, x[1], fmaf(q0.z, x[2], q0.w)));
+    float zr = q1.x * x[0] + q1.y * x[1] + q1.z * x[2];
+    float zg = q1.w * x[0] + q2.x * x[1] + q2.y * x[2];
+    float zb = q2.z * x[0] + q2.w * x[1] + q3.x * x[2];
+    zr = fmaf(q3.y, gam[0], zr);
+    zr = fmaf(q3.z, gam[1], zr);
+    zr = fmaf(q3.w, gam[2], zr);
+    asm volatile("" ::: "memory");
+    const float4 q4 = __ldg(p + 4), q5 = __ldg(p + 5), q6 = __ldg(p + 6);
+    zr = fmaf(q4.x, gam[3], zr);
+    zg = fmaf(q4.y, gam[0], zg);
+    zg = fmaf(q4.z, gam[1], zg);
+    zg = fmaf(q4.w, gam[2], zg);
+    zg = fmaf(q5.x, gam[3], zg);
+    zb = fmaf(q5.y, gam[0], zb);
+    zb = fmaf(q5.z, gam[1], zb);
+    zb = fmaf(q5.w, gam[2], zb);
+    zb = fmaf(q6.x, gam[3], zb);
+    f.a = q6.y;
+    f.b = q6.z;
+    f.sig = MODE == SALF_FIELD_EXP ? __expf(f.lin) : sdf_density(f.lin, f.a, f.b);
+    f.c[0] = sigmoidf_fast(zr);
+    f.c[1] = sigmoidf_fast(zg);
+    f.c[2] = sigmoidf_fast(zb);
+    f.io = 0.f;
+    if (want_int) {
+      const float4 q7 = __ldg(p + 7);
+      f.io = sigmoidf_fast(fmaf(q6.w, x[0], fmaf(q7.x, x[1], fmaf(q7.y, x[2], q7.z))));
+    }
+  } else {
+    Record<DT> rec;
+    rec.load(S.params, vox, want_int);
+    f.sig = density<MODE>(rec.v, x, &f.lin);
+    colour(rec.v, x, gam, f.c);
+    f.io = want_int ? intensity_field(rec.v, x) : 0.f;
+    f.a = rec.v[25];
+    f.b = rec.v[26];
+  }
+}
+
 // Warp tile -> request, pixel.
 __device__ __forceinline__ int find_request(const LaunchParams& P, int warp) {
   int r = 0;
