@@ -23,6 +23,10 @@
 #ifndef SALF_FWD_BLOCKS_COHERENT
 #define SALF_FWD_BLOCKS_COHERENT 7
 #endif
+// Sensor kinds (bit = salf_sensor_kind) that take the high-occupancy variant.
+#ifndef SALF_FWD_COHERENT_KINDS
+#define SALF_FWD_COHERENT_KINDS ((1 << SALF_PINHOLE) | (1 << SALF_RAYS_EXPLICIT))
+#endif
 #ifndef SALF_FWD_WPB_DIVERGENT
 #define SALF_FWD_WPB_DIVERGENT 8
 #endif
@@ -141,7 +145,7 @@ cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
   for (int i = 0; i < P.n_req; ++i) {
     const ReqDev& q = P.req[i];
     dump = dump || q.vcap > 0 || q.ray_dump || q.steps_out;
-    coherent = coherent && (q.kind == SALF_PINHOLE || q.kind == SALF_RAYS_EXPLICIT);
+    coherent = coherent && ((SALF_FWD_COHERENT_KINDS >> q.kind) & 1);
   }
   const int dt = P.S.dtype, md = P.S.mode;
   if (dt == SALF_F32 && md == SALF_FIELD_EXP)
