@@ -11,7 +11,9 @@
 // (d sigma / d s = a e^{-|s|/b} / (2b), d sigma / d a = sigma / a,
 //  d sigma / d b = -a s e^{-|s|/b} / (2 b^2)) and Eq. 2 (d c / d z = c (1 - c),
 // d z / d W_c = x, d z / d W_sh = gamma).  Gradients go to the caller's
-// input-order FP32 buffer with 16-byte vector atomics.
+// input-order FP32 buffer with 16-byte vector atomics; lanes of a warp that
+// hit the same voxel in the same round first sum their rows in shared memory,
+// so each voxel takes one set of atomics per warp and round.
 #include "traverse.cuh"
 
 using namespace salf;
@@ -63,12 +65,15 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ Launch
   const float gbg = g[0] * Q.bg[0] + g[1] * Q.bg[1] + g[2] * Q.bg[2];
   float T = 1.f, Pk = 0.f;
   int k = 0;
+  __shared__ float s_rows[SALF_WARPS_PER_BLOCK][32][33];  // padded: conflict-free columns
+  float(*rows)[33] = s_rows[threadIdx.x >> 5];
 
   const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   for (;;) {
     Hit h;
     const bool hit = next_hit(S, w, h, budget);
     if (!__any_sync(0xffffffffu, hit || w.alive)) break;
+    const unsigned hit_lanes = __ballot_sync(0xffffffffu, hit);
     if (hit) {
       const float tm = 0.5f * (h.tin + h.tout);
       const float dl = h.tout - h.tin;
@@ -115,11 +120,33 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ Launch
 #pragma unroll
         for (int q = 0; q < 4; ++q) gr[27 + q] = dz * xh[q];
       }
-      float4* dst = reinterpret_cast<float4*>(Q.d_params) + (size_t)__ldg(&S.order[h.vox]) * 8;
+      const int key = __ldg(&S.order[h.vox]);
+      const unsigned peers = __match_any_sync(hit_lanes, key);
+      const int leader = __ffs(peers) - 1;
+      const int nq = want_int ? 8 : 7;
+      if (peers != (1u << lane)) {
+        // several lanes hit this voxel: the lowest one sums their rows
 #pragma unroll
-      for (int q = 0; q < 7; ++q)
-        atomicAdd(dst + q, make_float4(gr[4 * q], gr[4 * q + 1], gr[4 * q + 2], gr[4 * q + 3]));
-      if (want_int) atomicAdd(dst + 7, make_float4(gr[28], gr[29], gr[30], gr[31]));
+        for (int q = 0; q < 32; ++q) rows[lane][q] = gr[q];
+        __syncwarp(peers);
+        if (lane == leader) {
+          unsigned rest = peers & (peers - 1u);
+          while (rest) {
+            const int l2 = __ffs(rest) - 1;
+            rest &= rest - 1u;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) gr[q] += rows[l2][q];
+          }
+        }
+        __syncwarp(peers);
+      }
+      if (lane == leader) {
+        float4* dst = reinterpret_cast<float4*>(Q.d_params) + (size_t)key * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nq)
+            atomicAdd(dst + q, make_float4(gr[4 * q], gr[4 * q + 1], gr[4 * q + 2], gr[4 * q + 3]));
+      }
       T = Tn;
       if (++k >= nv) w.alive = false;
     }

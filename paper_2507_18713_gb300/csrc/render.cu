@@ -6,10 +6,11 @@
 // density and Eq. 2 colour at each segment midpoint -> Eq. 3-4 front-to-back
 // compositing, stopping once the transmittance drops below t_min.
 //
-// The loop is "while-while": every live lane first walks (empty leaves are
-// skipped whole) to its next hit voxel, then the lanes that have one gather
-// their records and composite together; the warp leaves the loop when no lane
-// has a hit (ballot).  Lanes whose ray terminated early idle in the ballot.
+// Each round of the loop, every live lane takes at most `step_budget`
+// structure steps toward its next hit voxel (empty leaves are skipped whole),
+// then the lanes that have a hit gather their records and composite together;
+// the warp leaves the loop when no lane has work left (ballot).  Lanes whose
+// ray terminated early idle in the ballot.
 #include "traverse.cuh"
 
 // Warps per block and resident blocks per SM of each forward variant (they
@@ -67,32 +68,37 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dp = 0.f, Ip = 0.f;
   int nvis = 0;
 
+  // composite one hit voxel (Eq. 3-4) with its field at the segment midpoint
+  auto shade = [&](const Hit& h) {
+    const float tm = 0.5f * (h.tin + h.tout);
+    const float dl = h.tout - h.tin;
+    float x[3];
+    local_coords(w, h, tm, x);
+    Field f;
+    field_eval<DT, MODE>(S, h.vox, want_int, x, gam, f);
+    const float sig = f.sig, io = f.io;
+    const float* c = f.c;
+    const float e = __expf(-sig * dl);   // 1 - alpha (Eq. 4)
+    const float wgt = T * (1.f - e);     // T_i alpha_i (Eq. 3)
+    C0 = fmaf(wgt, c[0], C0);
+    C1 = fmaf(wgt, c[1], C1);
+    C2 = fmaf(wgt, c[2], C2);
+    Dp = fmaf(wgt, tm, Dp);
+    Ip = fmaf(wgt, io, Ip);
+    T *= e;
+    if (DUMP) {
+      if (nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + nvis] = __ldg(&S.order[h.vox]);
+    }
+    ++nvis;
+  };
+
   const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   for (;;) {
     Hit h;
     const bool hit = next_hit(S, w, h, budget);
     if (!__any_sync(0xffffffffu, hit || w.alive)) break;
     if (hit) {
-      const float tm = 0.5f * (h.tin + h.tout);
-      const float dl = h.tout - h.tin;
-      float x[3];
-      local_coords(w, h, tm, x);
-      Field f;
-      field_eval<DT, MODE>(S, h.vox, want_int, x, gam, f);
-      const float sig = f.sig, io = f.io;
-      const float* c = f.c;
-      const float e = __expf(-sig * dl);   // 1 - alpha (Eq. 4)
-      const float wgt = T * (1.f - e);     // T_i alpha_i (Eq. 3)
-      C0 = fmaf(wgt, c[0], C0);
-      C1 = fmaf(wgt, c[1], C1);
-      C2 = fmaf(wgt, c[2], C2);
-      Dp = fmaf(wgt, tm, Dp);
-      Ip = fmaf(wgt, io, Ip);
-      T *= e;
-      if (DUMP) {
-        if (nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + nvis] = __ldg(&S.order[h.vox]);
-      }
-      ++nvis;
+      shade(h);
       if (T < tmin) w.alive = false;
     }
   }

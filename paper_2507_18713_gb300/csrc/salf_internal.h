@@ -29,13 +29,15 @@
 // Acceleration structure (replaces the paper's pointer octree, Sec. III-B):
 //  * occupancy pyramid: mask level 0 has one 64-bit word per 4x4x4 block of
 //    level-0 cells (bit = Morton index of the cell inside the block) plus the
-//    rank offset of the block's first occupied cell in `entries`; mask level
+//    rank offset of the block's first occupied cell in `cells`; mask level
 //    m >= 1 has one word per 4x4x4 words of level m-1 (bit set iff that word
 //    is non-zero).  An empty cell is skipped together with the largest empty
 //    aligned pyramid cell that contains it (one slab exit per skip).
-//  * entries[rank] for each occupied level-0 cell: a voxel index (>= 0) or
-//    -2 - node for a subdivided cell; nodes hold 8 children with the same
-//    encoding (-1 = empty child).
+//  * cells[rank] = (e, cm) for each occupied level-0 cell.  cm == 0: e is a
+//    voxel index (>= 0) or -2 - node for a subdivided cell; nodes hold 8
+//    children with the same encoding (-1 = empty child).  cm != 0: the cell is
+//    split once into voxels; cm is the occupancy of its 8 children (bit =
+//    x | y << 1 | z << 2) and child c is voxel e + popcount(cm & ((1 << c) - 1)).
 //  * column pyramid: for every footprint of 2^c x 2^c level-0 columns, a
 //    128-bit mask of the z-layers (layer = layer_cells level-0 cells high)
 //    that hold any voxel.  A ray in an empty layer of a footprint can jump to
@@ -47,7 +49,7 @@ struct DevScene {
   const uint4* mask0;
   const unsigned long long* mask[SALF_MAX_MASK_LEVELS];
   int mdim[SALF_MAX_MASK_LEVELS][3];
-  const int* entries;
+  const int2* cells;
   const int* nodes;
   const uint4* col[SALF_MAX_COL_LEVELS];  // column masks per level: (lo64, hi64) as uint4
   int cdim[SALF_MAX_COL_LEVELS][2];

@@ -198,6 +198,28 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
     }
   }
   if (nodes.empty()) nodes.assign(8, -1);
+  // Device cell table: (entry, child mask).  A cell split exactly once, into
+  // children that are all voxels or empty, becomes (first child voxel, 8-bit
+  // occupancy of its children): the children are consecutive in Morton order,
+  // so the traversal finds a child without reading its node.
+  std::vector<int2> cells(entries.size());
+  for (size_t r = 0; r < entries.size(); ++r) {
+    const int32_t e = entries[r];
+    cells[r] = make_int2(e, 0);
+    if (e > -2) continue;
+    const int32_t* ch = &nodes[(size_t)(-2 - e) * 8];
+    unsigned cm = 0;
+    int32_t first = -1, expect = -1;
+    bool flat = true;
+    for (int c = 0; c < 8 && flat; ++c) {
+      if (ch[c] == -1) continue;
+      if (ch[c] < 0 || (expect >= 0 && ch[c] != expect)) flat = false;
+      if (first < 0) first = ch[c];
+      expect = ch[c] + 1;
+      cm |= 1u << c;
+    }
+    if (flat && cm) cells[r] = make_int2(first, (int)cm);
+  }
 
   // ---- upper pyramid levels
   std::vector<std::vector<uint64_t>> up(1);
@@ -291,15 +313,15 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
   }
   for (int m = 0; m < M; ++m)
     for (int a = 0; a < 3; ++a) D.mdim[m][a] = mdim[m][a];
-  int32_t* dentries = nullptr;
+  int2* dcells = nullptr;
   int32_t* dnodes = nullptr;
   int32_t* dorder = nullptr;
-  if ((st = upload(s, entries, &dentries)) != SALF_OK) return st;
+  if ((st = upload(s, cells, &dcells)) != SALF_OK) return st;
   if ((st = upload(s, nodes, &dnodes)) != SALF_OK) return st;
   std::vector<int32_t> ord = order;
   if (ord.empty()) ord.push_back(0);
   if ((st = upload(s, ord, &dorder)) != SALF_OK) return st;
-  D.entries = dentries;
+  D.cells = dcells;
   D.nodes = dnodes;
   D.order = dorder;
   for (int c = 0; c < CL; ++c) {

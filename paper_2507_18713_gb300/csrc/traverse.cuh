@@ -203,8 +203,15 @@ __device__ __forceinline__ int find_leaf(const DevScene& S, int ix, int iy, int 
   const unsigned long long m = ((unsigned long long)w.y << 32) | (unsigned long long)w.x;
   const unsigned bit = morton6(cx & 3, cy & 3, cz & 3);
   if ((m >> bit) & 1ull) {
-    int e = __ldg(&S.entries[w.z + __popcll(m & ((1ull << bit) - 1ull))]);
+    const int2 en = __ldg(&S.cells[w.z + __popcll(m & ((1ull << bit) - 1ull))]);
+    int e = en.x;
     int l = K;
+    if (en.y) {  // split once: child voxel by rank, no node read
+      l = K - 1;
+      const unsigned ch = ((ix >> l) & 1) | (((iy >> l) & 1) << 1) | (((iz >> l) & 1) << 2);
+      const unsigned cm = (unsigned)en.y;
+      e = ((cm >> ch) & 1u) ? e + __popc(cm & ((1u << ch) - 1u)) : -1;
+    }
     while (e <= -2) {
       --l;
       const int ch = ((ix >> l) & 1) | (((iy >> l) & 1) << 1) | (((iz >> l) & 1) << 2);
