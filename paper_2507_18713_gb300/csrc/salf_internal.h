@@ -29,7 +29,10 @@
 // Acceleration structure (replaces the paper's pointer octree, Sec. III-B):
 //  * occupancy pyramid: mask level 0 has one 64-bit word per 4x4x4 block of
 //    level-0 cells (bit = Morton index of the cell inside the block) plus the
-//    rank offset of the block's first occupied cell in `cells`; mask level
+//    rank offset of the block's first occupied cell in `cells` and, when
+//    every occupied cell of the block is one level-0 voxel, the index of the
+//    block's first voxel (voxels are numbered block by block, cells inside a
+//    block in bit order), else all ones; mask level
 //    m >= 1 has one word per 4x4x4 words of level m-1 (bit set iff that word
 //    is non-zero).  An empty cell is skipped together with the largest empty
 //    aligned pyramid cell that contains it (one slab exit per skip).
@@ -43,7 +46,8 @@
 //    that hold any voxel.  A ray in an empty layer of a footprint can jump to
 //    the nearest occupied layer in its direction of travel, or to the
 //    footprint's side, in one step.
-//  * params: records in Morton order of the voxel's min corner (FP32 or BF16);
+//  * params: records in voxel order (block, cell inside the block, Morton
+//    index of the min corner inside the cell), FP32 or BF16;
 //    order[internal] = input index.
 struct DevScene {
   const uint4* mask0;

@@ -1,5 +1,5 @@
 // scene_build.cpp -- salf_build_scene: validates the voxel set, sorts it in
-// Morton order, builds the occupancy pyramid / level-0 cell table /
+// block order, builds the occupancy pyramid / level-0 cell table /
 // subdivision nodes (the accelerator that stands in for the paper's octree,
 // Sec. III-B) and uploads everything to the device.
 #include <algorithm>
@@ -101,8 +101,17 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
   cudaError_t ce = cudaSetDevice(ctx->device);
   if (ce != cudaSuccess) return salf_cuda_fail(ce, "cudaSetDevice");
 
-  // ---- Morton keys of the min corners (finest units), validation
+  // ---- sort keys of the min corners (finest units), validation.  Voxels are
+  // numbered block by block: the linear index of the 4x4x4 block of level-0
+  // cells, then the Morton index of the level-0 cell inside the block, then
+  // the Morton index of the min corner inside that cell.  Within a block the
+  // level-0 voxels thus follow the occupancy bits, and a block whose occupied
+  // cells are all level-0 voxels maps cell -> voxel by a popcount.  Bits: the
+  // block index needs 3 (19 - K) at most, the rest 6 + 3 K, so 63 in all.
+  int mdim[SALF_MAX_MASK_LEVELS][3];
+  for (int a = 0; a < 3; ++a) mdim[0][a] = (d->dims[a] + 3) / 4;
   std::vector<uint64_t> code((size_t)n);
+  const uint64_t fine = (1ULL << K) - 1ULL;
   for (int64_t v = 0; v < n; ++v) {
     const int l = d->level[v];
     if (l > K) {
@@ -118,7 +127,11 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
       }
       f[a] = (uint64_t)c << (K - l);
     }
-    code[v] = morton3(f[0], f[1], f[2]);
+    const uint64_t c0[3] = {f[0] >> K, f[1] >> K, f[2] >> K};
+    const uint64_t blk =
+        ((c0[2] >> 2) * (uint64_t)mdim[0][1] + (c0[1] >> 2)) * (uint64_t)mdim[0][0] + (c0[0] >> 2);
+    code[v] = (blk << (6 + 3 * K)) | ((uint64_t)morton6(c0[0] & 3, c0[1] & 3, c0[2] & 3) << (3 * K)) |
+              morton3(f[0] & fine, f[1] & fine, f[2] & fine);
   }
   std::vector<int32_t> order((size_t)n);
   std::iota(order.begin(), order.end(), 0);
@@ -126,8 +139,9 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
     if (code[a] != code[b]) return code[a] < code[b];
     return d->level[a] < d->level[b];
   });
-  // A voxel of level l covers the Morton range [code, code + 8^(K-l)); in this
-  // order an overlap (duplicate, ancestor) always shows up between neighbours.
+  // A voxel of level l lies in one level-0 cell and covers the key range
+  // [code, code + 8^(K-l)); in this order an overlap (duplicate, ancestor)
+  // always shows up between neighbours.
   for (int64_t p = 1; p < n; ++p) {
     const int32_t a = order[p - 1], b = order[p];
     const uint64_t span = 1ULL << (3 * (K - d->level[a]));
@@ -139,10 +153,10 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
   }
 
   // ---- occupancy of level-0 cells, rank offsets, cell table, nodes
-  int mdim[SALF_MAX_MASK_LEVELS][3];
-  for (int a = 0; a < 3; ++a) mdim[0][a] = (d->dims[a] + 3) / 4;
   const int64_t nb0 = (int64_t)mdim[0][0] * mdim[0][1] * mdim[0][2];
   std::vector<uint64_t> m0((size_t)nb0, 0);
+  std::vector<uint32_t> vfirst((size_t)nb0, 0xffffffffu);
+  std::vector<uint8_t> split((size_t)nb0, 0);
   auto block_of = [&](int64_t cx, int64_t cy, int64_t cz) {
     return ((cz >> 2) * mdim[0][1] + (cy >> 2)) * mdim[0][0] + (cx >> 2);
   };
@@ -150,7 +164,10 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
     const int32_t v = order[p];
     const int l = d->level[v];
     const int64_t cx = d->ijk[3 * v] >> l, cy = d->ijk[3 * v + 1] >> l, cz = d->ijk[3 * v + 2] >> l;
-    m0[block_of(cx, cy, cz)] |= 1ULL << morton6(cx & 3, cy & 3, cz & 3);
+    const int64_t b = block_of(cx, cy, cz);
+    m0[b] |= 1ULL << morton6(cx & 3, cy & 3, cz & 3);
+    if (vfirst[b] == 0xffffffffu) vfirst[b] = (uint32_t)p;
+    if (l > 0) split[b] = 1;
   }
   std::vector<uint4> mask0((size_t)nb0);
   int64_t running = 0;
@@ -158,7 +175,9 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
     mask0[b].x = (unsigned)(m0[b] & 0xffffffffULL);
     mask0[b].y = (unsigned)(m0[b] >> 32);
     mask0[b].z = (unsigned)running;
-    mask0[b].w = 0;
+    // voxel of the block's first occupied cell when every occupied cell is
+    // one level-0 voxel, else all ones (look the cell up in `cells`)
+    mask0[b].w = (m0[b] && !split[b]) ? vfirst[b] : 0xffffffffu;
     running += __builtin_popcountll(m0[b]);
   }
   std::vector<int32_t> entries((size_t)std::max<int64_t>(running, 1), -1);
@@ -200,7 +219,7 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
   if (nodes.empty()) nodes.assign(8, -1);
   // Device cell table: (entry, child mask).  A cell split exactly once, into
   // children that are all voxels or empty, becomes (first child voxel, 8-bit
-  // occupancy of its children): the children are consecutive in Morton order,
+  // occupancy of its children): the children are consecutive in voxel order,
   // so the traversal finds a child without reading its node.
   std::vector<int2> cells(entries.size());
   for (size_t r = 0; r < entries.size(); ++r) {

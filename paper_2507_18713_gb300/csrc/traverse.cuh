@@ -203,7 +203,12 @@ __device__ __forceinline__ int find_leaf(const DevScene& S, int ix, int iy, int 
   const unsigned long long m = ((unsigned long long)w.y << 32) | (unsigned long long)w.x;
   const unsigned bit = morton6(cx & 3, cy & 3, cz & 3);
   if ((m >> bit) & 1ull) {
-    const int2 en = __ldg(&S.cells[w.z + __popcll(m & ((1ull << bit) - 1ull))]);
+    const unsigned pre = __popcll(m & ((1ull << bit) - 1ull));
+    if (w.w != 0xffffffffu) {  // block of level-0 voxels: no cell-table read
+      *ls = K;
+      return (int)(w.w + pre);
+    }
+    const int2 en = __ldg(&S.cells[w.z + pre]);
     int e = en.x;
     int l = K;
     if (en.y) {  // split once: child voxel by rank, no node read
