@@ -268,6 +268,41 @@ salf_status salf_render_backward(salf_scene* scene, const salf_sensor* sensor,
                                  const float* d_opacity, const float* d_intensity,
                                  float* d_params, void* stream);
 
+/*
+ * Tile rasterisation of a pinhole camera (Sec. III-B, "Tile-based
+ * Splatting"): every voxel is projected onto the image and listed in each
+ * 16 x 16-pixel tile its projection may cover; each tile's list is sorted
+ * front to back and composited by one thread block, with the records staged
+ * in shared memory.  Per pixel, a voxel's opacity comes from the exact length
+ * of the pixel's ray inside it and its colour from the field at that
+ * segment's midpoint (Eq. 1-6), as in salf_render_rays.
+ * Sort order: level-0 cells by their L1 cell distance from the camera's
+ * level-0 cell, then, inside a cell, octree children nearest-first relative
+ * to the camera.  For a point camera this order agrees with the order along
+ * every pixel ray, so the outputs equal salf_render_rays' for the same camera
+ * (the paper's splatting is allowed to approximate; this one does not).
+ * Sensor: SALF_PINHOLE with one pose for the frame (rolling_shutter = 0 or
+ * t1 <= t0); other sensors are rejected with SALF_ERR_INVALID.  Outputs as
+ * for salf_render_rays, device memory only (on_host, ray_dump and steps are
+ * rejected; visits/visit_count are supported).  The tile lists live in a
+ * scene-owned workspace that grows on demand (cudaMalloc); calls on one scene
+ * are serialised by a lock.  The call waits on `stream` once, for the number
+ * of (voxel, tile) pairs, then enqueues the sort and the tile kernel and
+ * returns.  `stats` (optional) receives the frame's counts.  Errors: INVALID,
+ * OOM, CUDA; INVALID also when the sort key (tile index and camera-order key)
+ * would need more than 64 bits.
+ */
+typedef struct {
+  int64_t visible_voxels;  /* voxels listed in at least one tile */
+  int64_t pairs;           /* (voxel, tile) list entries */
+  int32_t tiles;           /* 16 x 16 tiles of the image */
+  int32_t key_bits;        /* bits of the sort key (4 per radix pass) */
+} salf_raster_stats;
+
+salf_status salf_render_raster(salf_scene* scene, const salf_sensor* sensor,
+                               const salf_render_opts* opts, const salf_outputs* out,
+                               salf_raster_stats* stats, void* stream);
+
 /* Check the scene's device status word (synchronises the device).  Returns
  * SALF_ERR_DEVICE if a kernel hit an internal bound since the last check. */
 salf_status salf_scene_check(salf_scene* scene);

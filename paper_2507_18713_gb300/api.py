@@ -190,6 +190,44 @@ class Scene:
             res["_keep"] = keep
         return res
 
+    def render_raster(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                      want_intensity=False, visits_cap=0, outputs=("rgb", "depth", "opacity"),
+                      saved=False, valid=True, stream=None, out: dict | None = None,
+                      stats: dict | None = None) -> dict:
+        """salf_render_raster (tile rasterisation, pinhole cameras with one pose)
+        into (new or given) CUDA tensors; the same outputs as `render`.  Waits
+        on `stream` once (for the tile-list size).  `stats`, if given, receives
+        the frame's visible voxels, (voxel, tile) pairs, tiles and key bits."""
+        R = n_rays(sensor)
+        dev = torch.device("cuda", self.ctx.device)
+        res = {} if out is None else dict(out)
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,)}
+        for k in outputs:
+            if k not in res:
+                res[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
+        if saved and "saved" not in res:
+            res["saved"] = torch.empty((R, 8), dtype=torch.float32, device=dev)
+        if valid and "valid" not in res:
+            res["valid"] = torch.empty((R,), dtype=torch.uint8, device=dev)
+        if visits_cap > 0:
+            res.setdefault("visit_count", torch.empty((R,), dtype=torch.int32, device=dev))
+            res.setdefault("visits", torch.empty((R, visits_cap), dtype=torch.int32, device=dev))
+        o = L.Outputs()
+        for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits"):
+            if k in res:
+                setattr(o, k, res[k].data_ptr())
+        keep: list = []
+        s = sensor_struct(sensor, keep)
+        op = opts_struct(t_min, background, want_intensity, visits_cap)
+        st = L.RasterStats()
+        L.check(L.load().salf_render_raster(self._h, C.byref(s), C.byref(op), C.byref(o),
+                                            C.byref(st), _stream_ptr(stream)),
+                "salf_render_raster")
+        if stats is not None:
+            stats.update(visible_voxels=st.visible_voxels, pairs=st.pairs, tiles=st.tiles,
+                         key_bits=st.key_bits)
+        return res
+
     def render_host(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
                     want_intensity=False, outputs=("rgb", "depth", "opacity"), out=None,
                     stream=None) -> dict:

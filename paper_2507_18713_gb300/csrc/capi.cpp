@@ -56,6 +56,10 @@ extern "C" void salf_scene_destroy(salf_scene* s) {
   cudaDeviceSynchronize();
   for (void* p : s->allocations) cudaFree(p);
   if (s->staging) cudaFree(s->staging);
+  if (s->raster_vox) cudaFree(s->raster_vox);
+  if (s->raster_pairs) cudaFree(s->raster_pairs);
+  if (s->raster_count_host) cudaFreeHost(s->raster_count_host);
+  if (s->raster_done) cudaEventDestroy(s->raster_done);
   delete s;
 }
 
@@ -457,6 +461,59 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
   }
   if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return salf_cuda_fail(e, "render");
   return SALF_OK;
+}
+
+extern "C" salf_status salf_render_raster(salf_scene* sc, const salf_sensor* sen,
+                                         const salf_render_opts* opts, const salf_outputs* out,
+                                         salf_raster_stats* stats, void* stream) {
+  if (!sc || !sen || !out) {
+    g_err = "salf_render_raster: null argument";
+    return SALF_ERR_INVALID;
+  }
+  if (sen->kind != SALF_PINHOLE) {
+    g_err = "salf_render_raster: pinhole cameras only";
+    return SALF_ERR_INVALID;
+  }
+  if (sen->rolling_shutter && sen->t1 > sen->t0 && sen->height > 1) {
+    g_err = "salf_render_raster: one camera pose per frame (no rolling shutter)";
+    return SALF_ERR_INVALID;
+  }
+  if (sen->width > 65535 * 16 || sen->height > 65535 * 16) {
+    g_err = "salf_render_raster: image too large";
+    return SALF_ERR_INVALID;
+  }
+  const salf_render_opts o = opts ? *opts : default_opts();
+  if (out->on_host || out->ray_dump || out->steps) {
+    g_err = "salf_render_raster: device outputs only (no ray_dump or steps)";
+    return SALF_ERR_INVALID;
+  }
+  if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
+      !(o.visits_cap > 0 && out->visits)) {
+    g_err = "salf_render_raster: no output requested";
+    return SALF_ERR_INVALID;
+  }
+  if (o.visits_cap > 0 && (!out->visits || !out->visit_count)) {
+    g_err = "salf_render_raster: visits_cap > 0 needs visits and visit_count";
+    return SALF_ERR_INVALID;
+  }
+  if (misaligned(out->saved, 16)) {
+    g_err = "salf_render_raster: saved must be 16-byte aligned";
+    return SALF_ERR_INVALID;
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  ReqDev r;
+  salf_status st = salf_prepare_request(sc, sen, &o, &r);
+  if (st != SALF_OK) return st;
+  r.rgb = out->rgb;
+  r.depth = out->depth;
+  r.opacity = out->opacity;
+  r.intensity = out->intensity;
+  r.saved = out->saved;
+  r.valid = out->valid;
+  r.vcount = out->visit_count;
+  r.visits = out->visits;
+  return salf_raster_run(sc, r, sen->fx, sen->fy, stats, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* sen,

@@ -65,32 +65,7 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   sh_basis(r.d, gam);
   const bool want_int = Q.want_int != 0;
   const float tmin = Q.t_min;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dp = 0.f, Ip = 0.f;
-  int nvis = 0;
-
-  // composite one hit voxel (Eq. 3-4) with its field at the segment midpoint
-  auto shade = [&](const Hit& h) {
-    const float tm = 0.5f * (h.tin + h.tout);
-    const float dl = h.tout - h.tin;
-    float x[3];
-    local_coords(w, h, tm, x);
-    Field f;
-    field_eval<DT, MODE>(S, h.vox, want_int, x, gam, f);
-    const float sig = f.sig, io = f.io;
-    const float* c = f.c;
-    const float e = __expf(-sig * dl);   // 1 - alpha (Eq. 4)
-    const float wgt = T * (1.f - e);     // T_i alpha_i (Eq. 3)
-    C0 = fmaf(wgt, c[0], C0);
-    C1 = fmaf(wgt, c[1], C1);
-    C2 = fmaf(wgt, c[2], C2);
-    Dp = fmaf(wgt, tm, Dp);
-    Ip = fmaf(wgt, io, Ip);
-    T *= e;
-    if (DUMP) {
-      if (nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + nvis] = __ldg(&S.order[h.vox]);
-    }
-    ++nvis;
-  };
+  Accum A{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
 
   const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   for (;;) {
@@ -98,33 +73,23 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
     const bool hit = next_hit(S, w, h, budget);
     if (!__any_sync(0xffffffffu, hit || w.alive)) break;
     if (hit) {
-      shade(h);
-      if (T < tmin) w.alive = false;
+      const GlobalRec src{reinterpret_cast<const float4*>(S.params) +
+                          (size_t)h.vox * RecordLayout<DT>::kChunks};
+      composite_hit<DT, MODE>(w, h, src, want_int, gam, A);
+      if (DUMP) {
+        if (A.nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + A.nvis] = __ldg(&S.order[h.vox]);
+      }
+      ++A.nvis;
+      if (A.T < tmin) w.alive = false;
     }
   }
   if (!in_img) return;
-  const bool valid = r.valid;
-  const float Op = 1.f - T;  // sum of T_i alpha_i telescopes to 1 - T_end (Eq. 3-4)
-  if (Q.rgb) {
-    float* o = Q.rgb + 3 * (size_t)ray;
-    o[0] = valid ? fmaf(T, Q.bg[0], C0) : 0.f;
-    o[1] = valid ? fmaf(T, Q.bg[1], C1) : 0.f;
-    o[2] = valid ? fmaf(T, Q.bg[2], C2) : 0.f;
-  }
-  if (Q.depth) Q.depth[ray] = Dp;
-  if (Q.opacity) Q.opacity[ray] = Op;
-  if (Q.intensity) Q.intensity[ray] = Ip;
-  if (Q.saved) {
-    float4* s = reinterpret_cast<float4*>(Q.saved) + 2 * (size_t)ray;
-    s[0] = make_float4(C0, C1, C2, Dp);
-    s[1] = make_float4(Op, Ip, T, (float)nvis);
-  }
-  if (Q.valid) Q.valid[ray] = valid ? 1 : 0;
+  write_outputs(Q, ray, r.valid, A);
   if (DUMP) {
     if (Q.steps_out) Q.steps_out[ray] = w.steps;
     if (Q.vcap > 0) {
-      Q.vcount[ray] = nvis;
-      for (int k = nvis; k < Q.vcap; ++k) Q.visits[(size_t)ray * Q.vcap + k] = -1;
+      Q.vcount[ray] = A.nvis;
+      for (int k = A.nvis; k < Q.vcap; ++k) Q.visits[(size_t)ray * Q.vcap + k] = -1;
     }
   }
 }

@@ -48,7 +48,8 @@
 //    footprint's side, in one step.
 //  * params: records in voxel order (block, cell inside the block, Morton
 //    index of the min corner inside the cell), FP32 or BF16;
-//    order[internal] = input index.
+//    order[internal] = input index; vox_box[internal] = (min corner in finest
+//    cells, log2 of the edge in finest cells), read by the rasteriser.
 struct DevScene {
   const uint4* mask0;
   const unsigned long long* mask[SALF_MAX_MASK_LEVELS];
@@ -62,6 +63,7 @@ struct DevScene {
   int n_layers;     // <= 128
   const void* params;
   const int* order;
+  const int4* vox_box;
   int* status;
   double origin[3];
   double inv_sfin;  // finest cells per metre
@@ -149,6 +151,15 @@ struct salf_scene {
   std::mutex staging_mu;
   void* staging = nullptr;
   size_t staging_bytes = 0;
+  // rasteriser workspaces (grown on demand, guarded by raster_mu): per-voxel
+  // arrays, per-pair arrays, and a pinned word for the pair count
+  std::mutex raster_mu;
+  void* raster_vox = nullptr;
+  size_t raster_vox_bytes = 0;
+  void* raster_pairs = nullptr;
+  size_t raster_pairs_bytes = 0;
+  unsigned long long* raster_count_host = nullptr;
+  cudaEvent_t raster_done = nullptr;  // end of the last call's GPU work
 };
 
 // Implemented in the .cu / .cpp files of the library.
@@ -164,4 +175,8 @@ int salf_step_budget();
 cudaError_t salf_launch_gather_params(const float* in, const int* order, void* out, int64_t n,
                                       int dtype, int mode, int* status, cudaStream_t st);
 cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st);
+// Tile rasterisation of one pinhole request (r prepared by
+// salf_prepare_request, outputs set); fills *stats when non-null.
+salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double fy,
+                            salf_raster_stats* stats, cudaStream_t st);
 cudaError_t salf_launch_backward(const LaunchParams& P, cudaStream_t st);

@@ -343,6 +343,18 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
   D.cells = dcells;
   D.nodes = dnodes;
   D.order = dorder;
+  {
+    std::vector<int4> box((size_t)std::max<int64_t>(n, 1), make_int4(0, 0, 0, 0));
+    for (int64_t p = 0; p < n; ++p) {
+      const int32_t v = order[p];
+      const int l = d->level[v];
+      box[p] = make_int4((int)(d->ijk[3 * v] << (K - l)), (int)(d->ijk[3 * v + 1] << (K - l)),
+                         (int)(d->ijk[3 * v + 2] << (K - l)), K - l);
+    }
+    int4* dbox = nullptr;
+    if ((st = upload(s, box, &dbox)) != SALF_OK) return st;
+    D.vox_box = dbox;
+  }
   for (int c = 0; c < CL; ++c) {
     uint4* pc = nullptr;
     if ((st = upload(s, cols[c], &pc)) != SALF_OK) return st;

@@ -440,45 +440,30 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
 // ---------------------------------------------------------------- records
 
 template <int DT>
-struct Record;
+struct Record;  // widened record (BF16 only: FP32 records are read in stages)
 
-// FP32: 32 floats (128 B).  Loads what the field needs: floats 0..27 always
-// (W_sigma/W_s, W_c, W_sh, a, b), 28..31 only with intensity.
-template <>
-struct Record<SALF_F32> {
-  float v[32];
-  __device__ __forceinline__ void load(const void* base, int vox, bool intensity) {
-    const float4* p = reinterpret_cast<const float4*>(base) + (size_t)vox * 8;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      float4 q = __ldg(p + k);
-      v[4 * k] = q.x;
-      v[4 * k + 1] = q.y;
-      v[4 * k + 2] = q.z;
-      v[4 * k + 3] = q.w;
-    }
-    if (intensity) {
-      float4 q = __ldg(p + 7);
-      v[28] = q.x;
-      v[29] = q.y;
-      v[30] = q.z;
-      v[31] = q.w;
-    } else {
-      v[28] = v[29] = v[30] = v[31] = 0.f;
-    }
-  }
+// Where a record's 16-byte chunks come from: global memory (read-only path)
+// or a copy of the raw record bytes in shared memory.
+struct GlobalRec {
+  const float4* p;
+  __device__ __forceinline__ float4 chunk(int k) const { return __ldg(p + k); }
+};
+struct SharedRec {
+  const float4* p;
+  __device__ __forceinline__ float4 chunk(int k) const { return p[k]; }
 };
 
 // BF16: 32 bf16 (64 B), widened to FP32 in registers.
 template <>
 struct Record<SALF_BF16> {
   float v[32];
-  __device__ __forceinline__ void load(const void* base, int vox, bool intensity) {
-    const uint4* p = reinterpret_cast<const uint4*>(base) + (size_t)vox * 4;
-    (void)intensity;  // every 16-byte chunk holds a used scalar
+  template <class Src>
+  __device__ __forceinline__ void load(const Src& src) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      uint4 q = __ldg(p + k);
+      const float4 c = src.chunk(k);
+      const uint4 q = make_uint4(__float_as_uint(c.x), __float_as_uint(c.y), __float_as_uint(c.z),
+                                 __float_as_uint(c.w));
       unsigned w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -578,12 +563,11 @@ __device__ __forceinline__ float sdf_density(float s, float a, float b) {
 // stage's loads below the first stage's arithmetic), so only half of the
 // record is live in registers at a time.  Slots: Wsigma 0-3, W_c 4-12 (rows
 // r, g, b), W_sh 13-24 (rows r, g, b), a 25, b 26, W_int 27-30.
-template <int DT, int MODE>
-__device__ __forceinline__ void field_eval(const DevScene& S, int vox, bool want_int,
-                                           const float x[3], const float gam[4], Field& f) {
-  if (DT == SALF_F32) {
-    const float4* p = reinterpret_cast<const float4*>(S.params) + (size_t)vox * 8;
-    const float4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2), q3 = __ldg(p + 3);
+template <int DT, int MODE, class Src>
+__device__ __forceinline__ void field_eval_src(const Src& p, bool want_int, const float x[3],
+                                               const float gam[4], Field& f) {
+  if constexpr (DT == SALF_F32) {
+    const float4 q0 = p.chunk(0), q1 = p.chunk(1), q2 = p.chunk(2), q3 = p.chunk(3);
     f.lin = fmaf(q0.x, x[0], fmaf(q0.y, x[1], fmaf(q0.z, x[2], q0.w)));
     float zr = q1.x * x[0] + q1.y * x[1] + q1.z * x[2];
     float zg = q1.w * x[0] + q2.x * x[1] + q2.y * x[2];
@@ -592,7 +576,7 @@ __device__ __forceinline__ void field_eval(const DevScene& S, int vox, bool want
     zr = fmaf(q3.z, gam[1], zr);
     zr = fmaf(q3.w, gam[2], zr);
     asm volatile("" ::: "memory");
-    const float4 q4 = __ldg(p + 4), q5 = __ldg(p + 5), q6 = __ldg(p + 6);
+    const float4 q4 = p.chunk(4), q5 = p.chunk(5), q6 = p.chunk(6);
     zr = fmaf(q4.x, gam[3], zr);
     zg = fmaf(q4.y, gam[0], zg);
     zg = fmaf(q4.z, gam[1], zg);
@@ -610,18 +594,81 @@ __device__ __forceinline__ void field_eval(const DevScene& S, int vox, bool want
     f.c[2] = sigmoidf_fast(zb);
     f.io = 0.f;
     if (want_int) {
-      const float4 q7 = __ldg(p + 7);
+      const float4 q7 = p.chunk(7);
       f.io = sigmoidf_fast(fmaf(q6.w, x[0], fmaf(q7.x, x[1], fmaf(q7.y, x[2], q7.z))));
     }
   } else {
     Record<DT> rec;
-    rec.load(S.params, vox, want_int);
+    rec.load(p);
     f.sig = density<MODE>(rec.v, x, &f.lin);
     colour(rec.v, x, gam, f.c);
     f.io = want_int ? intensity_field(rec.v, x) : 0.f;
     f.a = rec.v[25];
     f.b = rec.v[26];
   }
+}
+
+// Record bytes per voxel and the 16-byte chunks of one record.
+template <int DT>
+struct RecordLayout {
+  static constexpr int kChunks = DT == SALF_F32 ? 8 : 4;
+};
+
+template <int DT, int MODE>
+__device__ __forceinline__ void field_eval(const DevScene& S, int vox, bool want_int,
+                                           const float x[3], const float gam[4], Field& f) {
+  const GlobalRec src{reinterpret_cast<const float4*>(S.params) +
+                      (size_t)vox * RecordLayout<DT>::kChunks};
+  field_eval_src<DT, MODE>(src, want_int, x, gam, f);
+}
+
+// Front-to-back accumulators of one ray (Eq. 3-4).
+struct Accum {
+  float T, C0, C1, C2, Dp, Ip;
+  int nvis;
+};
+
+// Composite one hit voxel with its field at the segment midpoint: alpha =
+// 1 - exp(-sigma delta) (Eq. 4), weight T alpha (Eq. 3).  The ray kernel and
+// the tile rasteriser both call this, so their arithmetic is the same.
+template <int DT, int MODE, class Src>
+__device__ __forceinline__ void composite_hit(const Walk& w, const Hit& h, const Src& src,
+                                              bool want_int, const float gam[4], Accum& A) {
+  const float tm = 0.5f * (h.tin + h.tout);
+  const float dl = h.tout - h.tin;
+  float x[3];
+  local_coords(w, h, tm, x);
+  Field f;
+  field_eval_src<DT, MODE>(src, want_int, x, gam, f);
+  const float e = __expf(-f.sig * dl);  // 1 - alpha (Eq. 4)
+  const float wgt = A.T * (1.f - e);    // T_i alpha_i (Eq. 3)
+  A.C0 = fmaf(wgt, f.c[0], A.C0);
+  A.C1 = fmaf(wgt, f.c[1], A.C1);
+  A.C2 = fmaf(wgt, f.c[2], A.C2);
+  A.Dp = fmaf(wgt, tm, A.Dp);
+  A.Ip = fmaf(wgt, f.io, A.Ip);
+  A.T *= e;
+}
+
+// Per-ray outputs of a request (colour premultiplied, background added with
+// the final transmittance; opacity 1 - T_end, which the weights sum to).
+__device__ __forceinline__ void write_outputs(const ReqDev& Q, int ray, bool valid, const Accum& A) {
+  if (Q.rgb) {
+    float* o = Q.rgb + 3 * (size_t)ray;
+    o[0] = valid ? fmaf(A.T, Q.bg[0], A.C0) : 0.f;
+    o[1] = valid ? fmaf(A.T, Q.bg[1], A.C1) : 0.f;
+    o[2] = valid ? fmaf(A.T, Q.bg[2], A.C2) : 0.f;
+  }
+  const float Op = 1.f - A.T;  // sum of T_i alpha_i telescopes to 1 - T_end (Eq. 3-4)
+  if (Q.depth) Q.depth[ray] = A.Dp;
+  if (Q.opacity) Q.opacity[ray] = Op;
+  if (Q.intensity) Q.intensity[ray] = A.Ip;
+  if (Q.saved) {
+    float4* s = reinterpret_cast<float4*>(Q.saved) + 2 * (size_t)ray;
+    s[0] = make_float4(A.C0, A.C1, A.C2, A.Dp);
+    s[1] = make_float4(Op, A.Ip, A.T, (float)A.nvis);
+  }
+  if (Q.valid) Q.valid[ray] = valid ? 1 : 0;
 }
 
 // Warp tile -> request, pixel.
