@@ -33,9 +33,13 @@ using namespace salf;
 
 namespace {
 
+#ifndef SALF_RASTER_MIN_BLOCKS
+#define SALF_RASTER_MIN_BLOCKS 3  // resident tile blocks per SM the register budget allows
+#endif
+
 constexpr int kTile = 16;          // tile edge in pixels
 constexpr int kRasterThreads = kTile * kTile;
-constexpr int kChunk = 64;         // voxels staged in shared memory at a time
+constexpr int kChunk = 128;        // voxels staged in shared memory at a time
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -54,6 +58,7 @@ struct ProjParams {
   int dig_shift;      // 3 K: bits of the octree digits
   unsigned* count;    // tiles per voxel
   uint2* rect;        // tile rectangle (x0 | y0 << 16, x1 | y1 << 16)
+  int4* prect;        // pixel rectangle (u0, u1, v0, v1), inclusive
   unsigned long long* key;
   unsigned long long* n_visible;  // voxels listed in at least one tile
 };
@@ -99,6 +104,7 @@ __device__ __forceinline__ unsigned project_one(const ProjParams& G, int p) {
   }
   unsigned cnt = 0;
   uint2 rc = make_uint2(0, 0);
+  int4 pr = make_int4(1, 0, 1, 0);  // empty
   if (front) {
     // box points close to the camera plane project without bound, in the
     // direction of where the box's edges cross that plane
@@ -127,10 +133,12 @@ __device__ __forceinline__ unsigned project_one(const ProjParams& G, int p) {
       const int tx0 = u0 / kTile, tx1 = u1 / kTile, ty0 = v0 / kTile, ty1 = v1 / kTile;
       cnt = (unsigned)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
       rc = make_uint2((unsigned)tx0 | ((unsigned)ty0 << 16), (unsigned)tx1 | ((unsigned)ty1 << 16));
+      pr = make_int4(u0, u1, v0, v1);
     }
   }
   G.count[p] = cnt;
   G.rect[p] = rc;
+  G.prect[p] = pr;
   // camera-order key
   const int K = G.S.K;
   unsigned l1 = 0;
@@ -380,21 +388,27 @@ struct RasterParams {
   ReqDev Q;
   const uint2* ranges;
   const unsigned* vox;
+  const int4* prect;  // per voxel: pixel rectangle its projection may cover
   int tiles_x;
 };
 
 template <int DT, int MODE, bool DUMP>
-__global__ void __launch_bounds__(kRasterThreads) k_raster(const __grid_constant__ RasterParams RP) {
+__global__ void __launch_bounds__(kRasterThreads, SALF_RASTER_MIN_BLOCKS) k_raster(const __grid_constant__ RasterParams RP) {
   constexpr int RQ = RecordLayout<DT>::kChunks;
   __shared__ float4 s_rec[kChunk * RQ];
   __shared__ float s_pl[kChunk][6];  // plane offsets: (lo - Oi) - Of, (hi - Oi) - Of per axis
   __shared__ int4 s_box[kChunk];
+  __shared__ int4 s_prect[kChunk];
   __shared__ int s_vox[kChunk];
   const DevScene& S = RP.S;
   const ReqDev& Q = RP.Q;
   const int tile = blockIdx.x;
+  const int lane = threadIdx.x & 31;
   const int u = (tile % RP.tiles_x) * kTile + (threadIdx.x % kTile);
   const int v = (tile / RP.tiles_x) * kTile + (threadIdx.x / kTile);
+  // this warp's pixels: 16 columns x 2 rows
+  const int strip_u0 = (tile % RP.tiles_x) * kTile, strip_u1 = strip_u0 + kTile - 1;
+  const int strip_v0 = (tile / RP.tiles_x) * kTile + 2 * (threadIdx.x >> 5), strip_v1 = strip_v0 + 1;
   const bool in_img = u < Q.W && v < Q.H;
   const int ray = v * Q.W + u;
 
@@ -426,34 +440,74 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(const __grid_constant
       const unsigned vx = __ldg(&RP.vox[c0 + j]);
       s_rec[i] = __ldg(reinterpret_cast<const float4*>(S.params) + (size_t)vx * RQ + k);
     }
-    if (threadIdx.x < n) {
-      const unsigned vx = __ldg(&RP.vox[c0 + threadIdx.x]);
+    for (int i = threadIdx.x; i < n; i += kRasterThreads) {
+      const unsigned vx = __ldg(&RP.vox[c0 + i]);
       const int4 b = __ldg(&S.vox_box[vx]);
       const int E = 1 << b.w;
       const int lo[3] = {b.x, b.y, b.z};
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        s_pl[threadIdx.x][a] = (float)(lo[a] - Q.Oi[a]) - Q.Of[a];
-        s_pl[threadIdx.x][3 + a] = (float)(lo[a] + E - Q.Oi[a]) - Q.Of[a];
+        s_pl[i][a] = (float)(lo[a] - Q.Oi[a]) - Q.Of[a];
+        s_pl[i][3 + a] = (float)(lo[a] + E - Q.Oi[a]) - Q.Of[a];
       }
-      s_box[threadIdx.x] = b;
-      s_vox[threadIdx.x] = (int)vx;
+      s_box[i] = b;
+      s_prect[i] = __ldg(&RP.prect[vx]);
+      s_vox[i] = (int)vx;
     }
     __syncthreads();
-    if (w.alive) {
-      for (int j = 0; j < n; ++j) {
-        // slab test with the ray kernel's expressions (same plane values)
-        float tx[3], tin = t0;
+    // voxels whose pixel rectangle meets this warp's 16 x 2 pixel strip
+    unsigned sel[kChunk / 32];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float pe = pos[a] ? s_pl[j][3 + a] : s_pl[j][a];
-          const float pn = pos[a] ? s_pl[j][a] : s_pl[j][3 + a];
-          tx[a] = pe * w.invD[a];
-          tin = fmaxf(tin, pn * w.invD[a]);
-        }
-        const int ax = (tx[0] <= tx[1] && tx[0] <= tx[2]) ? 0 : (tx[1] <= tx[2] ? 1 : 2);
-        const float tout = fminf(tx[ax], w.tend);
-        if (tout > tin) {
+    for (int q = 0; q < kChunk / 32; ++q) {
+      const int j = q * 32 + lane;
+      bool meet = false;
+      if (j < n) {
+        const int4 pr = s_prect[j];
+        meet = pr.x <= strip_u1 && pr.y >= strip_u0 && pr.z <= strip_v1 && pr.w >= strip_v0;
+      }
+      sel[q] = __ballot_sync(0xffffffffu, meet);
+    }
+    // slab test with the ray kernel's expressions (same plane values)
+    auto slab = [&](int j, float* tin_out, float* tout_out) {
+      float tx[3], tin = t0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float pe = pos[a] ? s_pl[j][3 + a] : s_pl[j][a];
+        const float pn = pos[a] ? s_pl[j][a] : s_pl[j][3 + a];
+        tx[a] = pe * w.invD[a];
+        tin = fmaxf(tin, pn * w.invD[a]);
+      }
+      const int ax = (tx[0] <= tx[1] && tx[0] <= tx[2]) ? 0 : (tx[1] <= tx[2] ? 1 : 2);
+      *tin_out = tin;
+      *tout_out = fminf(tx[ax], w.tend);
+    };
+    // phase 1: which of the strip's voxels this pixel's ray crosses
+    unsigned hits[kChunk / 32];
+#pragma unroll
+    for (int q = 0; q < kChunk / 32; ++q) {
+      hits[q] = 0u;
+      unsigned m = w.alive ? sel[q] : 0u;
+      while (m) {
+        const int jj = __ffs(m) - 1;
+        m &= m - 1;
+        const int j = q * 32 + jj;
+        const int4 pr = s_prect[j];  // outside it, the ray misses the box
+        if (u < pr.x || u > pr.y || v < pr.z || v > pr.w) continue;
+        float tin, tout;
+        slab(j, &tin, &tout);
+        if (tout > tin) hits[q] |= 1u << jj;
+      }
+    }
+    // phase 2: the lanes composite their next hit together, in list order
+#pragma unroll
+    for (int q = 0; q < kChunk / 32; ++q) {
+      while (__any_sync(0xffffffffu, w.alive && hits[q] != 0u)) {
+        if (w.alive && hits[q]) {
+          const int jj = __ffs(hits[q]) - 1;
+          hits[q] &= hits[q] - 1;
+          const int j = q * 32 + jj;
+          float tin, tout;
+          slab(j, &tin, &tout);
           const int4 b = s_box[j];
           Hit h;
           h.vox = s_vox[j];
@@ -468,10 +522,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(const __grid_constant
             if (A.nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + A.nvis] = __ldg(&S.order[h.vox]);
           }
           ++A.nvis;
-          if (A.T < tmin) {
-            w.alive = false;
-            break;
-          }
+          if (A.T < tmin) w.alive = false;
         }
       }
     }
@@ -545,8 +596,8 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
   const long long nn = std::max(n, 1LL);
   const size_t b_count = align256(nn * 4), b_rect = align256(nn * 8), b_key = align256(nn * 8),
                b_offs = align256((nn + 2) * 8), b_tmp = align256(scan_tmp_elems(nn) * 8),
-               b_ranges = align256((size_t)ntiles * 8);
-  const size_t need_vox = b_count + b_rect + b_key + b_offs + b_tmp + b_ranges;
+               b_ranges = align256((size_t)ntiles * 8), b_prect = align256(nn * 16);
+  const size_t need_vox = b_count + b_rect + b_key + b_offs + b_tmp + b_ranges + b_prect;
   if (sc->raster_vox_bytes < need_vox) {
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return salf_cuda_fail(e, "raster sync");
     if ((e = cudaEventSynchronize(sc->raster_done)) != cudaSuccess)
@@ -575,6 +626,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
   unsigned long long* stmp =
       reinterpret_cast<unsigned long long*>(wv + b_count + b_rect + b_key + b_offs);
   uint2* ranges = reinterpret_cast<uint2*>(wv + b_count + b_rect + b_key + b_offs + b_tmp);
+  int4* prect = reinterpret_cast<int4*>(wv + b_count + b_rect + b_key + b_offs + b_tmp + b_ranges);
 
   unsigned long long P = 0, visible = 0;
   if (n > 0) {
@@ -598,6 +650,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     G.dig_shift = 3 * K;
     G.count = count;
     G.rect = rect;
+    G.prect = prect;
     G.key = vkey;
     G.n_visible = offs + n + 1;
     if ((e = cudaMemsetAsync(offs + n + 1, 0, 8, st)) != cudaSuccess)
@@ -680,6 +733,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
   RP.Q = r;
   RP.ranges = ranges;
   RP.vox = vals;
+  RP.prect = prect;
   RP.tiles_x = tiles_x;
   const bool dump = r.vcap > 0;
   if (S.dtype == SALF_F32 && S.mode == SALF_FIELD_EXP)
