@@ -7,7 +7,7 @@
 //     and its camera-order key;
 //  2. exclusive scan of the tile counts -> each voxel's slot range;
 //  3. k_emit: one (tile | key, voxel) pair per touched tile;
-//  4. stable LSD radix sort of the pairs, 4 bits per pass;
+//  4. stable LSD radix sort of the pairs, 8 bits per pass;
 //  5. k_tile_ranges: each tile's slice of the sorted pairs;
 //  6. k_raster: one 256-thread block per tile, one thread per pixel; the
 //     tile's voxels are staged 64 at a time in shared memory (records raw,
@@ -44,8 +44,10 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;      // per thread, contiguous (keeps the scatter stable)
+constexpr int kSortItems = 8;      // rounds per block
 constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
 
 struct ProjParams {
   DevScene S;
@@ -284,89 +286,77 @@ cudaError_t scan_exclusive(const Tin* in, long long n, Tout* out, Tout* tmp, cud
 }
 
 // ---------------------------------------------------------------- radix sort
+//
+// LSD radix sort of the pairs, 8 bits per pass.  A block owns kSortTile
+// consecutive items, read in rounds of kSortThreads (round r, thread t holds
+// item r * kSortThreads + t), so the order of (round, thread) is the input
+// order and the scatter below keeps it among equal digits (stable).
 
-// Digit counts of each block's tile (hist[digit * nblk + block]).
+// Digit counts of each block's items (hist[digit * nblk + block]).
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long long* __restrict__ keys,
                                                              long long n, int shift,
                                                              unsigned* __restrict__ hist, int nblk) {
-  __shared__ unsigned h[16];
-  if (threadIdx.x < 16) h[threadIdx.x] = 0;
+  __shared__ unsigned h[kRadix];
+  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) h[d] = 0;
   __syncthreads();
-  const long long i0 = (long long)blockIdx.x * kSortTile + (long long)threadIdx.x * kSortItems;
-  unsigned long long cnt = 0;  // 16 packed 4-bit counters (at most 8 items each)
+  const long long base = (long long)blockIdx.x * kSortTile;
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k)
-    if (i0 + k < n) cnt += 1ull << (4 * (unsigned)((keys[i0 + k] >> shift) & 15ull));
-#pragma unroll
-  for (int d = 0; d < 16; ++d) {
-    const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)((cnt >> (4 * d)) & 15ull));
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&h[d], c);
+  for (int r = 0; r < kSortItems; ++r) {
+    const long long i = base + (long long)r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & (kRadix - 1)], 1u);
   }
   __syncthreads();
-  if (threadIdx.x < 16) hist[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d * nblk + blockIdx.x] = h[d];
 }
 
-// Stable scatter: item (block, thread, k) goes to
-// scanned_hist[digit][block] + (earlier threads' items with that digit) + (its
-// rank among this thread's items with that digit).
+// Stable scatter: item goes to scanned_hist[digit][block] + (items of this
+// block before it with the same digit).  Per round, lanes with equal digits
+// are ranked inside their warp (match), and warps are ranked per digit
+// through shared counts.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const unsigned long long* __restrict__ kin, const unsigned* __restrict__ vin,
     unsigned long long* __restrict__ kout, unsigned* __restrict__ vout, long long n, int shift,
     const unsigned* __restrict__ hoff, int nblk) {
-  __shared__ unsigned s[16][kSortThreads + 1];
-  const long long i0 = (long long)blockIdx.x * kSortTile + (long long)threadIdx.x * kSortItems;
-  unsigned long long key[kSortItems];
-  unsigned val[kSortItems];
-  unsigned long long cnt = 0;
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    if (i0 + k < n) {
-      key[k] = kin[i0 + k];
-      val[k] = vin[i0 + k];
-      cnt += 1ull << (4 * (unsigned)((key[k] >> shift) & 15ull));
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ unsigned s_base[kRadix];          // running count per digit (earlier rounds)
+  __shared__ unsigned s_warp[kWarps][kRadix];  // this round: count, then exclusive prefix
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
+    s_base[d] = hoff[d * nblk + blockIdx.x];
+  const long long base = (long long)blockIdx.x * kSortTile;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kSortItems; ++r) {
+    const long long i = base + (long long)r * kSortThreads + threadIdx.x;
+    const bool ok = i < n;
+    unsigned long long key = 0;
+    unsigned val = 0;
+    if (ok) {
+      key = kin[i];
+      val = vin[i];
     }
-  }
+    const unsigned d = ok ? (unsigned)(key >> shift) & (kRadix - 1) : (unsigned)kRadix;
+    __syncthreads();  // the previous round's prefixes have been read
+    for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) (&s_warp[0][0])[k] = 0;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned rank = __popc(peers & lt);
+    if (ok && rank == 0) s_warp[wid][d] = __popc(peers);
+    __syncthreads();
+    for (int dd = threadIdx.x; dd < kRadix; dd += kSortThreads) {
+      unsigned run = s_base[dd];
 #pragma unroll
-  for (int d = 0; d < 16; ++d) s[d][threadIdx.x] = (unsigned)((cnt >> (4 * d)) & 15ull);
-  __syncthreads();
-  // exclusive scan over threads of each digit's counts: warp w scans digits 2w, 2w + 1
-  {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int dd = 0; dd < 2; ++dd) {
-      const int d = 2 * wid + dd;
-      constexpr int per = kSortThreads / 32;
-      unsigned loc[per], sum = 0;
-#pragma unroll
-      for (int j = 0; j < per; ++j) {
-        loc[j] = s[d][lane * per + j];
-        sum += loc[j];
+      for (int w = 0; w < kWarps; ++w) {
+        const unsigned c = s_warp[w][dd];
+        s_warp[w][dd] = run;
+        run += c;
       }
-      unsigned x = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      unsigned run = x - sum;
-#pragma unroll
-      for (int j = 0; j < per; ++j) {
-        s[d][lane * per + j] = run;
-        run += loc[j];
-      }
+      s_base[dd] = run;
     }
-  }
-  __syncthreads();
-  unsigned long long seen = 0;
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    if (i0 + k < n) {
-      const unsigned d = (unsigned)((key[k] >> shift) & 15ull);
-      const unsigned pos = hoff[d * nblk + blockIdx.x] + s[d][threadIdx.x] +
-                           (unsigned)((seen >> (4 * d)) & 15ull);
-      seen += 1ull << (4 * d);
-      kout[pos] = key[k];
-      vout[pos] = val[k];
+    __syncthreads();
+    if (ok) {
+      const unsigned pos = s_warp[wid][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
     }
   }
 }
@@ -590,7 +580,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     return SALF_ERR_INVALID;
   }
   const int key_bits = low_bits + tile_bits;
-  const int passes = (key_bits + 3) / 4;
+  const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
 
   // per-voxel workspace
   const long long nn = std::max(n, 1LL);
@@ -673,7 +663,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
 
   // per-pair workspace
   const long long nblk = (long long)((P + kSortTile - 1) / kSortTile);
-  const long long hn = 16 * std::max(nblk, 1LL);
+  const long long hn = (long long)kRadix * std::max(nblk, 1LL);
   const size_t pp = std::max<unsigned long long>(P, 1);
   const size_t b_k = align256(pp * 8), b_v = align256(pp * 4), b_h = align256(hn * 4),
                b_ht = align256(scan_tmp_elems(hn) * 4);
@@ -712,7 +702,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     unsigned long long *ki = kA, *ko = kB;
     unsigned *vi = vA, *vo = vB;
     for (int pass = 0; pass < passes; ++pass) {
-      const int shift = 4 * pass;
+      const int shift = kRadixBits * pass;
       k_radix_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(ki, (long long)P, shift, hist,
                                                             (int)nblk);
       if ((e = scan_exclusive<unsigned, unsigned>(hist, hn, hoff, htmp, st)) != cudaSuccess)
