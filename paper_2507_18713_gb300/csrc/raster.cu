@@ -39,7 +39,10 @@ namespace {
 
 constexpr int kTile = 16;          // tile edge in pixels
 constexpr int kRasterThreads = kTile * kTile;
-constexpr int kChunk = 128;        // voxels staged in shared memory at a time
+#ifndef SALF_RASTER_CHUNK
+#define SALF_RASTER_CHUNK 128
+#endif
+constexpr int kChunk = SALF_RASTER_CHUNK;  // voxels staged in shared memory at a time
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -385,7 +388,8 @@ struct RasterParams {
 template <int DT, int MODE, bool DUMP>
 __global__ void __launch_bounds__(kRasterThreads, SALF_RASTER_MIN_BLOCKS) k_raster(const __grid_constant__ RasterParams RP) {
   constexpr int RQ = RecordLayout<DT>::kChunks;
-  __shared__ float4 s_rec[kChunk * RQ];
+  constexpr int RS = RQ + 1;  // padded record stride: lanes reading different records hit different banks
+  __shared__ float4 s_rec[kChunk * RS];
   __shared__ float s_pl[kChunk][6];  // plane offsets: (lo - Oi) - Of, (hi - Oi) - Of per axis
   __shared__ int4 s_box[kChunk];
   __shared__ int4 s_prect[kChunk];
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(kRasterThreads, SALF_RASTER_MIN_BLOCKS) k_rast
     for (int i = threadIdx.x; i < n * RQ; i += kRasterThreads) {
       const int j = i / RQ, k = i % RQ;
       const unsigned vx = __ldg(&RP.vox[c0 + j]);
-      s_rec[i] = __ldg(reinterpret_cast<const float4*>(S.params) + (size_t)vx * RQ + k);
+      s_rec[j * RS + k] = __ldg(reinterpret_cast<const float4*>(S.params) + (size_t)vx * RQ + k);
     }
     for (int i = threadIdx.x; i < n; i += kRasterThreads) {
       const unsigned vx = __ldg(&RP.vox[c0 + i]);
@@ -507,7 +511,7 @@ __global__ void __launch_bounds__(kRasterThreads, SALF_RASTER_MIN_BLOCKS) k_rast
           h.base[2] = b.z;
           h.tin = tin;
           h.tout = tout;
-          composite_hit<DT, MODE>(w, h, SharedRec{&s_rec[j * RQ]}, want_int, gam, A);
+          composite_hit<DT, MODE>(w, h, SharedRec{&s_rec[j * RS]}, want_int, gam, A);
           if (DUMP) {
             if (A.nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + A.nvis] = __ldg(&S.order[h.vox]);
           }
