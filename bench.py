@@ -39,6 +39,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCES = ["paper_2507_18713_gb300/csrc/render.cu", "paper_2507_18713_gb300/csrc/traverse.cuh",
                   "paper_2507_18713_gb300/csrc/salf_internal.h"]
+RASTER_SOURCES = KERNEL_SOURCES + ["paper_2507_18713_gb300/csrc/raster.cu"]
 FALLBACK_HBM_GBS = 6800.0
 
 # algorithmic bytes (Eq. 1-2 record scalars read per visit, outputs per ray)
@@ -49,9 +50,11 @@ B_OUT_CAMERA = 20
 B_OUT_LIDAR = 12
 
 
-def kernel_hash() -> str:
+def kernel_hash(workload: str = "camera") -> str:
+    """Hash of the sources of the kernel a workload times (ncu traffic figures
+    are only used while it matches)."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (RASTER_SOURCES if workload == "raster" else KERNEL_SOURCES):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -90,6 +93,12 @@ WORKLOADS = {
                     want_intensity=False, outputs=("rgb", "depth", "opacity"),
                     metric="Mrays/s (valid rays), 1080p 190-degree fisheye, 2M-voxel driving scene",
                     workload="equidistant fisheye 1920x1080 190deg, driving scene 2,000,000 voxels"),
+    "raster": dict(sensor=driving_camera, b_field=B_FIELD_EXP_F32, b_out=B_OUT_CAMERA,
+                   want_intensity=False, outputs=("rgb", "depth", "opacity"),
+                   metric="Mrays/s, 1080p pinhole camera by tile rasterisation, 2M-voxel driving "
+                          "scene (FP32, forward)",
+                   workload=WORKLOAD + ", tile rasteriser (projection, tile lists, radix sort, "
+                            "16x16 tiles)"),
 }
 
 
@@ -426,8 +435,9 @@ def main():
     ap.add_argument("--impl", default="salf", choices=["salf", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
-    ap.add_argument("--workload", default="camera", choices=["camera", "lidar", "fisheye"],
-                    help="sensor of the headline line (default: the 1080p camera)")
+    ap.add_argument("--workload", default="camera", choices=["camera", "lidar", "fisheye", "raster"],
+                    help="sensor of the headline line (default: the 1080p camera by ray "
+                         "casting; raster: the same camera by tile rasterisation)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -458,7 +468,15 @@ def main():
     outs = wl["outputs"]
     R = cam["width"] * cam["height"]
     out = {k: torch.empty((R, 3) if k == "rgb" else (R,), device="cuda") for k in outs}
-    fn = lambda: g.render(cam, out=out, outputs=outs, valid=False, want_intensity=want_int)
+    raster = args.workload == "raster"
+    if raster:
+        fn = lambda: g.render_raster(cam, out=out, outputs=outs, valid=False)
+        rstats = {}
+        g.render_raster(cam, out=out, outputs=outs, valid=False, stats=rstats)
+        launches_per_step = rstats["kernels"]
+    else:
+        fn = lambda: g.render(cam, out=out, outputs=outs, valid=False, want_intensity=want_int)
+        launches_per_step = 1
 
     sampler = ClockSampler(gpu_id_for(torch, local))
     for _ in range(args.warmup):
@@ -489,21 +507,32 @@ def main():
     achieved = bytes_alg / (avg * 1e-3) / 1e9
     traffic = None
     try:
-        tj = json.load(open(TRAFFIC_FILE))
-        if tj.get("kernel_hash") == kernel_hash():
-            traffic = tj.get("dram_bytes_per_launch", {}).get(args.workload)
+        ent = json.load(open(TRAFFIC_FILE)).get(args.workload, {})
+        if ent.get("kernel_hash") == kernel_hash(args.workload):
+            traffic = ent.get("dram_bytes_per_launch")
     except Exception:
         pass
 
     # end to end through the C ABI with host output buffers (pinned)
     host = {k: torch.empty((R, 3) if k == "rgb" else (R,), dtype=torch.float32, pin_memory=True)
             for k in outs}
+    if raster:  # device outputs, then copies into the pinned host buffers
+        def e2e_call():
+            g.render_raster(cam, out=out, outputs=outs, valid=False)
+            for k in outs:
+                host[k].copy_(out[k], non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_how = "salf_render_raster, then copies of the outputs into pinned host buffers"
+    else:
+        def e2e_call():
+            g.render_host(cam, out=host, want_intensity=want_int)
+        e2e_how = "salf_render_rays with pinned host output buffers, synchronous"
     for _ in range(args.warmup):
-        g.render_host(cam, out=host, want_intensity=want_int)
+        e2e_call()
     e2e_steps = max(10, args.steps // 4)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        g.render_host(cam, out=host, want_intensity=want_int)
+        e2e_call()
     e2e_s = time.perf_counter() - t0
     e2e_value = world * n_counted * e2e_steps / e2e_s / 1e6
 
@@ -517,13 +546,14 @@ def main():
                               frac=achieved / peak, traffic=traffic,
                               peak_source=f"{peak_kind} hbm_gbs",
                               bytes_per_launch=bytes_alg,
-                              kernel="k_forward<F32,EXP>",
+                              kernel="k_raster<F32,EXP> (whole pipeline timed)" if raster
+                              else "k_forward<F32,EXP>",
                               note="bytes = visits x record scalars read + outputs per ray; "
                                    "visits counted by the kernel"),
                 e2e=dict(value=e2e_value, unit="Mrays/s", h2d_bytes_per_step=0,
                          d2h_bytes_per_step=R * 4 * (len(outs) + 2 * ("rgb" in outs)),
-                         how="salf_render_rays with pinned host output buffers, synchronous"),
-                gpu_launches=args.steps, clocks=clocks)
+                         how=e2e_how),
+                gpu_launches=args.steps * launches_per_step, clocks=clocks)
 
     if not args.no_extras and rank == 0:
         def extra(name, fn):

@@ -297,6 +297,8 @@ typedef struct {
   int64_t pairs;           /* (voxel, tile) list entries */
   int32_t tiles;           /* 16 x 16 tiles of the image */
   int32_t key_bits;        /* bits of the sort key (8 per radix pass) */
+  int32_t kernels;         /* kernel launches of the call */
+  int32_t reserved;
 } salf_raster_stats;
 
 salf_status salf_render_raster(salf_scene* scene, const salf_sensor* sensor,

@@ -65,7 +65,7 @@ class ServeStats(C.Structure):
 
 class RasterStats(C.Structure):
     _fields_ = [("visible_voxels", c_int64), ("pairs", c_int64), ("tiles", c_int32),
-                ("key_bits", c_int32)]
+                ("key_bits", c_int32), ("kernels", c_int32), ("reserved", c_int32)]
 
 
 # Every symbol include/salf.h declares, with its ctypes signature.

@@ -225,7 +225,7 @@ class Scene:
                 "salf_render_raster")
         if stats is not None:
             stats.update(visible_voxels=st.visible_voxels, pairs=st.pairs, tiles=st.tiles,
-                         key_bits=st.key_bits)
+                         key_bits=st.key_bits, kernels=st.kernels)
         return res
 
     def render_host(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),

@@ -274,16 +274,19 @@ long long scan_tmp_elems(long long n) {
 }
 
 template <class Tin, class Tout>
-cudaError_t scan_exclusive(const Tin* in, long long n, Tout* out, Tout* tmp, cudaStream_t st) {
+cudaError_t scan_exclusive(const Tin* in, long long n, Tout* out, Tout* tmp, cudaStream_t st,
+                           int* launches) {
   if (n <= 0) return cudaSuccess;
   const long long nb = (n + kScanTile - 1) / kScanTile;
   Tout* bsum = tmp;
   Tout* boff = tmp + nb;
   k_scan_tiles<Tin, Tout><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, out, bsum);
+  ++*launches;
   if (nb > 1) {
-    cudaError_t e = scan_exclusive<Tout, Tout>(bsum, nb, boff, tmp + 2 * nb, st);
+    cudaError_t e = scan_exclusive<Tout, Tout>(bsum, nb, boff, tmp + 2 * nb, st, launches);
     if (e != cudaSuccess) return e;
     k_scan_add<Tout><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, boff);
+    ++*launches;
   }
   return cudaGetLastError();
 }
@@ -532,6 +535,7 @@ __global__ void __launch_bounds__(kRasterThreads, SALF_RASTER_MIN_BLOCKS) k_rast
 
 template <int DT, int MODE>
 void launch_raster(const RasterParams& RP, int ntiles, bool dump, cudaStream_t st) {
+  if (ntiles <= 0) return;
   if (dump)
     k_raster<DT, MODE, true><<<ntiles, kRasterThreads, 0, st>>>(RP);
   else
@@ -623,6 +627,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
   int4* prect = reinterpret_cast<int4*>(wv + b_count + b_rect + b_key + b_offs + b_tmp + b_ranges);
 
   unsigned long long P = 0, visible = 0;
+  int launches = 0;
   if (n > 0) {
     ProjParams G;
     std::memset(&G, 0, sizeof(G));
@@ -650,9 +655,11 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     if ((e = cudaMemsetAsync(offs + n + 1, 0, 8, st)) != cudaSuccess)
       return salf_cuda_fail(e, "raster counter");
     k_project<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G);
-    if ((e = scan_exclusive<unsigned, unsigned long long>(count, n, offs, stmp, st)) != cudaSuccess)
+    if ((e = scan_exclusive<unsigned, unsigned long long>(count, n, offs, stmp, st, &launches)) !=
+        cudaSuccess)
       return salf_cuda_fail(e, "raster scan");
     k_scan_total<unsigned, unsigned long long><<<1, 1, 0, st>>>(count, n, offs);
+    launches += 2;
     if ((e = cudaMemcpyAsync(sc->raster_count_host, offs + n, 16, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
       return salf_cuda_fail(e, "raster count copy");
@@ -703,16 +710,19 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
   if (P > 0) {
     k_emit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(count, rect, vkey, offs, (int)n, tiles_x,
                                                           low_bits, kA, vA);
+    ++launches;
     unsigned long long *ki = kA, *ko = kB;
     unsigned *vi = vA, *vo = vB;
     for (int pass = 0; pass < passes; ++pass) {
       const int shift = kRadixBits * pass;
       k_radix_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(ki, (long long)P, shift, hist,
                                                             (int)nblk);
-      if ((e = scan_exclusive<unsigned, unsigned>(hist, hn, hoff, htmp, st)) != cudaSuccess)
+      if ((e = scan_exclusive<unsigned, unsigned>(hist, hn, hoff, htmp, st, &launches)) !=
+          cudaSuccess)
         return salf_cuda_fail(e, "raster sort scan");
       k_radix_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(ki, vi, ko, vo, (long long)P, shift,
                                                                hoff, (int)nblk);
+      launches += 2;
       std::swap(ki, ko);
       std::swap(vi, vo);
     }
@@ -720,6 +730,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     vals = vi;
     k_tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(keys, (long long)P, low_bits,
                                                                ranges);
+    ++launches;
   }
   RasterParams RP;
   std::memset(&RP, 0, sizeof(RP));
@@ -738,6 +749,7 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     launch_raster<SALF_BF16, SALF_FIELD_EXP>(RP, ntiles, dump, st);
   else
     launch_raster<SALF_BF16, SALF_FIELD_SDF>(RP, ntiles, dump, st);
+  launches += ntiles > 0 ? 1 : 0;
   if ((e = cudaGetLastError()) != cudaSuccess) return salf_cuda_fail(e, "raster launch");
   if ((e = cudaEventRecord(sc->raster_done, st)) != cudaSuccess)
     return salf_cuda_fail(e, "raster event");
@@ -746,6 +758,8 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     stats->tiles = ntiles;
     stats->key_bits = key_bits;
     stats->visible_voxels = (int64_t)visible;
+    stats->kernels = launches;
+    stats->reserved = 0;
   }
   return SALF_OK;
 }

@@ -37,7 +37,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(L.Outputs) == 10 * 8 + 8
     # kind,width,height + 7 floats = 40 -> pad to 8 -> 2*96 poses -> t0,t1 -> int + 2 floats -> ptr
     assert ctypes.sizeof(L.Sensor) == 40 + 192 + 16 + 12 + 4 + 8
-    assert ctypes.sizeof(L.RasterStats) == 8 + 8 + 4 + 4
+    assert ctypes.sizeof(L.RasterStats) == 8 + 8 + 4 + 4 + 4 + 4
 
 
 def test_no_gpu_means_a_clean_error():
