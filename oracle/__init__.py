@@ -11,6 +11,7 @@ from .oracle import (  # noqa: F401
     build,
     library_path,
     render,
+    render_actors,
     backward,
     gen_rays,
     trace,

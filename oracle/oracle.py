@@ -63,6 +63,11 @@ class _Outputs(C.Structure):
                 ("visits_cap", C.c_int32)]
 
 
+class _Actor(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("pose0", C.c_double * 12), ("pose1", C.c_double * 12),
+                ("id_base", C.c_int32)]
+
+
 class _Hit(C.Structure):
     _fields_ = [("voxel", C.c_int32), ("t_in", C.c_double), ("t_out", C.c_double)]
 
@@ -92,6 +97,8 @@ def _load():
             lib.orc_backward.argtypes = [vp, C.POINTER(_Sensor), C.POINTER(_Opts), vp, i64, vp,
                                          vp, vp, vp, vp]
             lib.orc_num_threads.restype = C.c_int
+            lib.orc_render_actors.argtypes = [vp, vp, i32, C.POINTER(_Sensor), C.POINTER(_Opts),
+                                              vp, i64, C.POINTER(_Outputs)]
             _lib = lib
     return _lib
 
@@ -298,3 +305,37 @@ def backward(oscene, sensor, g_rgb=None, g_depth=None, g_opacity=None, g_intensi
         raise RuntimeError(f"oracle backward failed: {st}")
     del keep
     return grad
+
+
+def render_actors(oscene, actors, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                  want_intensity=False, brute_force=False, visits_cap=0):
+    """Render with dynamic actors (Sec. IV-A) in FP64.  `actors`: list of
+    (OracleScene, pose0, pose1, id_base); poses are 3x4 canonical -> world at
+    the sensor's t0 / t1."""
+    lib = _load()
+    s, keep = _sensor(sensor)
+    idx, m = _idx(sensor, idx)
+    arr = (_Actor * max(1, len(actors)))()
+    for k, (osc, p0, p1, base) in enumerate(actors):
+        arr[k].scene = osc._h
+        arr[k].pose0[:] = [float(v) for v in np.asarray(p0, dtype=np.float64).ravel()]
+        arr[k].pose1[:] = [float(v) for v in np.asarray(p1, dtype=np.float64).ravel()]
+        arr[k].id_base = int(base)
+    o = _Outputs()
+    res = dict(rgb=np.zeros((m, 3)), depth=np.zeros(m), opacity=np.zeros(m),
+               intensity=np.zeros(m), t_end=np.zeros(m), term_gap=np.zeros(m),
+               n_visits=np.zeros(m, np.int32), valid=np.zeros(m, np.uint8))
+    for k, v in res.items():
+        setattr(o, k, _ptr(v))
+    if visits_cap > 0:
+        res["visits"] = np.full((m, visits_cap), -1, np.int32)
+        o.visits = _ptr(res["visits"])
+        o.visits_cap = int(visits_cap)
+    opt = _opts(t_min, background, want_intensity, brute_force)
+    st = lib.orc_render_actors(oscene._h, C.cast(arr, C.c_void_p), len(actors), C.byref(s),
+                               C.byref(opt), _ptr(idx), m, C.byref(o))
+    if st != 0:
+        raise RuntimeError(f"oracle actor render failed: {st}")
+    del keep
+    res["valid"] = res["valid"].astype(bool)
+    return res

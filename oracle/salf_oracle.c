@@ -448,21 +448,20 @@ static void quat_to_mat(const double q[4], double R[9]) {
   R[8] = 1 - 2 * (x * x + y * y);
 }
 
-/* Pose at time tau: linear translation, spherical-linear rotation between
- * pose0 (t0) and pose1 (t1).  At the start time the pose is pose0 itself. */
-void orc_pose_at(const orc_sensor* sen, double tau, double R[9], double t[3]) {
-  double s = 0.0;
-  if (sen->t1 > sen->t0) s = (tau - sen->t0) / (sen->t1 - sen->t0);
+/* Pose at fraction s of the way from pose0 to pose1 (3x4 row-major): linear
+ * translation, spherical-linear rotation.  At s = 0 the pose is pose0 itself. */
+static void interp_pose(const double* pose0, const double* pose1, double s, double R[9],
+                        double t[3]) {
   if (s == 0.0) {
     for (int r = 0; r < 3; ++r) {
-      for (int c = 0; c < 3; ++c) R[3 * r + c] = sen->pose0[4 * r + c];
-      t[r] = sen->pose0[4 * r + 3];
+      for (int c = 0; c < 3; ++c) R[3 * r + c] = pose0[4 * r + c];
+      t[r] = pose0[4 * r + 3];
     }
     return;
   }
   double q0[4], q1[4], q[4];
-  mat_to_quat(sen->pose0, q0);
-  mat_to_quat(sen->pose1, q1);
+  mat_to_quat(pose0, q0);
+  mat_to_quat(pose1, q1);
   double dot = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2] + q0[3] * q1[3];
   if (dot < 0) {
     dot = -dot;
@@ -482,7 +481,17 @@ void orc_pose_at(const orc_sensor* sen, double tau, double R[9], double t[3]) {
     for (int i = 0; i < 4; ++i) q[i] = a * q0[i] + b * q1[i];
   }
   quat_to_mat(q, R);
-  for (int r = 0; r < 3; ++r) t[r] = (1 - s) * sen->pose0[4 * r + 3] + s * sen->pose1[4 * r + 3];
+  for (int r = 0; r < 3; ++r) t[r] = (1 - s) * pose0[4 * r + 3] + s * pose1[4 * r + 3];
+}
+
+static double time_fraction(const orc_sensor* sen, double tau) {
+  return sen->t1 > sen->t0 ? (tau - sen->t0) / (sen->t1 - sen->t0) : 0.0;
+}
+
+/* Pose at time tau: linear translation, spherical-linear rotation between
+ * pose0 (t0) and pose1 (t1).  At the start time the pose is pose0 itself. */
+void orc_pose_at(const orc_sensor* sen, double tau, double R[9], double t[3]) {
+  interp_pose(sen->pose0, sen->pose1, time_fraction(sen, tau), R, t);
 }
 
 static void one_ray(const orc_sensor* sen, int64_t r, double o[3], double d[3], double* tn,
@@ -831,6 +840,134 @@ int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
     free(gq);
     free(suf);
     rr_free(&rr);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dynamic actors (Sec. IV-A)                                                */
+/* ------------------------------------------------------------------------ */
+/* Each actor is a voxel set in its own canonical frame, placed in the world
+ * by its pose at the ray's time (interpolated like the sensor's pose between
+ * the sensor's t0 and t1).  A ray is moved into every actor's frame (a rigid
+ * map: distances along the ray are unchanged), each frame's voxels are
+ * traced, and all hits are composited by Eq. 3-4 in order of entry, each
+ * with its field evaluated in its own frame (local coordinates and view
+ * direction of the actor's canonical frame). */
+
+typedef struct {
+  int32_t frame, voxel;
+  double t_in, t_out, key;
+} mhit;
+
+static int mhit_cmp(const void* pa, const void* pb) {
+  const mhit* a = (const mhit*)pa;
+  const mhit* b = (const mhit*)pb;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  if (a->frame != b->frame) return a->frame < b->frame ? -1 : 1;
+  return a->voxel < b->voxel ? -1 : (a->voxel > b->voxel);
+}
+
+int orc_render_actors(const orc_scene* s, const orc_actor* actors, int32_t n_actors,
+                      const orc_sensor* sen, const orc_opts* opt, const int64_t* idx, int64_t m,
+                      const orc_outputs* out) {
+  if (sen->width <= 0 || sen->height <= 0 || n_actors < 0) return 1;
+  const int nf = 1 + n_actors;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t r = idx ? idx[i] : i;
+    double o[3], d[3], tn, tf, tau;
+    uint8_t valid;
+    one_ray(sen, r, o, d, &tn, &tf, &tau, &valid);
+    double C[3] = {0, 0, 0}, D = 0, O = 0, I = 0, T = 1.0, gap = INFINITY;
+    int64_t nv = 0;
+    const double sfr = time_fraction(sen, tau);
+    /* the ray in every frame: frame 0 = world (static scene), frame 1 + k = actor k */
+    double* fo = (double*)malloc((size_t)nf * 3 * sizeof(double));
+    double* fd = (double*)malloc((size_t)nf * 3 * sizeof(double));
+    for (int a = 0; a < 3; ++a) {
+      fo[a] = o[a];
+      fd[a] = d[a];
+    }
+    for (int k = 0; k < n_actors; ++k) {
+      double R[9], t[3], rel[3];
+      interp_pose(actors[k].pose0, actors[k].pose1, sfr, R, t);
+      for (int a = 0; a < 3; ++a) rel[a] = o[a] - t[a];
+      for (int c = 0; c < 3; ++c) { /* R maps canonical -> world; its transpose maps back */
+        fo[3 * (1 + k) + c] = R[c] * rel[0] + R[3 + c] * rel[1] + R[6 + c] * rel[2];
+        fd[3 * (1 + k) + c] = R[c] * d[0] + R[3 + c] * d[1] + R[6 + c] * d[2];
+      }
+    }
+    mhit* mh = NULL;
+    int64_t nh = 0, ch = 0;
+    if (valid) {
+      for (int f = 0; f < nf; ++f) {
+        const orc_scene* sc = f == 0 ? s : actors[f - 1].scene;
+        hitvec hv = {0, 0, 0};
+        trace_vec(sc, fo + 3 * f, fd + 3 * f, tn, tf, opt->brute_force, &hv);
+        for (int64_t q = 0; q < hv.n; ++q) {
+          if (nh == ch) {
+            ch = ch ? 2 * ch : 64;
+            mh = (mhit*)realloc(mh, (size_t)ch * sizeof(mhit));
+          }
+          mh[nh].frame = f;
+          mh[nh].voxel = hv.h[q].voxel;
+          mh[nh].t_in = hv.h[q].t_in;
+          mh[nh].t_out = hv.h[q].t_out;
+          mh[nh].key = dmax(hv.h[q].t_in, tn);
+          ++nh;
+        }
+        free(hv.h);
+      }
+      if (nh > 1) qsort(mh, (size_t)nh, sizeof(mhit), mhit_cmp);
+      for (int64_t k = 0; k < nh; ++k) {
+        const int f = mh[k].frame;
+        const orc_scene* sc = f == 0 ? s : actors[f - 1].scene;
+        const double* of = fo + 3 * f;
+        const double* df = fd + 3 * f;
+        double lo[3], hi[3], e;
+        voxel_box(sc, mh[k].voxel, lo, hi, &e);
+        double a = dmax(mh[k].t_in, tn), b = dmin(mh[k].t_out, tf);
+        double tm = 0.5 * (a + b), dl = b - a;
+        double x[3];
+        for (int ax = 0; ax < 3; ++ax)
+          x[ax] = (of[ax] + tm * df[ax] - 0.5 * (lo[ax] + hi[ax])) / (0.5 * e);
+        double sig, c[3], io;
+        orc_field(sc->params + (size_t)REC * mh[k].voxel, sc->mode, x, df, &sig, c, &io);
+        if (!opt->want_intensity) io = 0.0;
+        double alpha = 1.0 - exp(-sig * dl); /* Eq. 4 */
+        double w = T * alpha;                /* Eq. 3 */
+        for (int q = 0; q < 3; ++q) C[q] += w * c[q];
+        D += w * tm;
+        O += w;
+        I += w * io;
+        if (out->visits && nv < out->visits_cap)
+          out->visits[i * out->visits_cap + nv] =
+              f == 0 ? mh[k].voxel : actors[f - 1].id_base + mh[k].voxel;
+        ++nv;
+        T = T * (1.0 - alpha);
+        if (opt->t_min > 0) {
+          double g = fabs(log(T) - log(opt->t_min));
+          if (g < gap) gap = g;
+          if (T < opt->t_min) break;
+        }
+      }
+      for (int q = 0; q < 3; ++q) C[q] += T * opt->background[q];
+    }
+    if (out->rgb)
+      for (int q = 0; q < 3; ++q) out->rgb[3 * i + q] = valid ? C[q] : 0.0;
+    if (out->depth) out->depth[i] = D;
+    if (out->opacity) out->opacity[i] = O;
+    if (out->intensity) out->intensity[i] = I;
+    if (out->t_end) out->t_end[i] = valid ? T : 1.0;
+    if (out->term_gap) out->term_gap[i] = gap;
+    if (out->n_visits) out->n_visits[i] = (int32_t)nv;
+    if (out->valid) out->valid[i] = valid;
+    if (out->visits)
+      for (int64_t k = nv; k < out->visits_cap; ++k) out->visits[i * out->visits_cap + k] = -1;
+    free(mh);
+    free(fo);
+    free(fd);
   }
   return 0;
 }

@@ -114,6 +114,25 @@ int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
                  const double* g_opacity, const double* g_intensity, double* grad);
 int orc_num_threads(void);
 
+/* Dynamic actors (Sec. IV-A): an actor is a voxel set in its own canonical
+ * frame (an orc_scene built from it), placed in the world by pose0 / pose1
+ * (canonical -> world, 3x4 row-major) at the sensor's t0 / t1 and by their
+ * interpolation (linear translation, slerp) at a ray's time.  The static
+ * scene's hits and every actor's hits (traced in the actor's frame) are
+ * composited together in order of entry (ties: static first, then actors in
+ * list order, then voxel index); each hit's field uses local coordinates and
+ * view direction of its own frame.  Visits report static voxels by input
+ * index and actor k's voxels as id_base + input index. */
+typedef struct {
+  const orc_scene* scene;
+  double pose0[12], pose1[12];
+  int32_t id_base;
+} orc_actor;
+
+int orc_render_actors(const orc_scene* s, const orc_actor* actors, int32_t n_actors,
+                      const orc_sensor* sen, const orc_opts* opt, const int64_t* idx, int64_t m,
+                      const orc_outputs* out);
+
 #ifdef __cplusplus
 }
 #endif

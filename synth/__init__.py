@@ -18,6 +18,7 @@ from .scenes import (  # noqa: F401
     single_voxel_scene,
     shuffle_scene,
 )
+from .actors import actor_shell, actor_tracks  # noqa: F401
 from .sensors import (  # noqa: F401
     pinhole,
     fisheye,
