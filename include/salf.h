@@ -305,6 +305,42 @@ salf_status salf_render_raster(salf_scene* scene, const salf_sensor* sensor,
                                const salf_render_opts* opts, const salf_outputs* out,
                                salf_raster_stats* stats, void* stream);
 
+/*
+ * Dynamic actors (Sec. IV-A).  An actor is a voxel set in its own canonical
+ * frame, built as a scene with salf_build_scene (same device, dtype and field
+ * mode as the static scene).  A request places each actor by pose0 / pose1:
+ * canonical -> world 3x4 row-major maps at the sensor's t0 / t1.  A ray at
+ * time fraction s of the exposure sees the actor at the pose interpolated
+ * like the sensor's (linear translation, geodesic rotation); for sensors
+ * without per-ray time, s = 0.  Per ray, the static voxels' hits and every
+ * actor's hits are composited together in order of entry (Eq. 3-4, early
+ * termination; the static hit first on ties).  An actor hit's field (Eq. 1-2,
+ * 5-6) uses the actor's canonical frame for its local coordinates and for the
+ * SH view direction.  The boxes of the actors' voxels must be pairwise
+ * disjoint at t0 and at t1 (SALF_ERR_OVERLAP otherwise), so along a ray at
+ * most one actor is open at a time.  A ray keeps the 8 nearest actor boxes it
+ * meets (more sets a device status bit, see salf_scene_check).
+ * Outputs as for salf_render_rays, device memory only (visits report actor
+ * voxels as id_base + the voxel's input index in its actor scene).  The actor
+ * table travels in a scene-owned device buffer (grown on demand; calls on one
+ * scene are ordered on the GPU).  Asynchronous on `stream`.  Errors: INVALID
+ * (sizes, more than SALF_MAX_ACTORS actors, null or mismatched actor scenes),
+ * OVERLAP, OOM, CUDA.
+ */
+#define SALF_MAX_ACTORS 256
+
+typedef struct {
+  const salf_scene* actor;      /* voxels in the actor's canonical frame */
+  double pose0[12], pose1[12];  /* canonical -> world at the sensor's t0 / t1 */
+  int32_t id_base;              /* visit id offset of this actor's voxels */
+  int32_t reserved;
+} salf_actor;
+
+salf_status salf_render_rays_actors(salf_scene* scene, const salf_actor* actors,
+                                    int32_t n_actors, const salf_sensor* sensor,
+                                    const salf_render_opts* opts, const salf_outputs* out,
+                                    void* stream);
+
 /* Check the scene's device status word (synchronises the device).  Returns
  * SALF_ERR_DEVICE if a kernel hit an internal bound since the last check. */
 salf_status salf_scene_check(salf_scene* scene);

@@ -63,6 +63,11 @@ class ServeStats(C.Structure):
                 ("p99_ms", c_double), ("max_ms", c_double), ("peak_bytes", c_int64)]
 
 
+class Actor(C.Structure):
+    _fields_ = [("actor", c_void_p), ("pose0", c_double * 12), ("pose1", c_double * 12),
+                ("id_base", c_int32), ("reserved", c_int32)]
+
+
 class RasterStats(C.Structure):
     _fields_ = [("visible_voxels", c_int64), ("pairs", c_int64), ("tiles", c_int32),
                 ("key_bits", c_int32), ("kernels", c_int32), ("reserved", c_int32)]
@@ -78,6 +83,8 @@ SIGNATURES = {
     "salf_scene_update_params": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
     "salf_render_rays": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts), C.POINTER(Outputs),
                           c_void_p], c_int32),
+    "salf_render_rays_actors": ([c_void_p, C.POINTER(Actor), c_int32, C.POINTER(Sensor),
+                                 C.POINTER(RenderOpts), C.POINTER(Outputs), c_void_p], c_int32),
     "salf_render_raster": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),
                             C.POINTER(Outputs), C.POINTER(RasterStats), c_void_p], c_int32),
     "salf_render_rays_host_noalloc": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),

@@ -228,6 +228,45 @@ class Scene:
                          key_bits=st.key_bits, kernels=st.kernels)
         return res
 
+    def render_actors(self, sensor: dict, actors, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                      want_intensity=False, visits_cap=0, outputs=("rgb", "depth", "opacity"),
+                      saved=False, valid=True, stream=None, out: dict | None = None) -> dict:
+        """salf_render_rays_actors: this scene plus dynamic actors.  `actors` is a
+        list of (Scene, pose0, pose1, id_base) with 3x4 canonical -> world poses
+        at the sensor's t0 and t1.  Asynchronous on `stream`."""
+        R = n_rays(sensor)
+        dev = torch.device("cuda", self.ctx.device)
+        res = {} if out is None else dict(out)
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,)}
+        for k in outputs:
+            if k not in res:
+                res[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
+        if saved and "saved" not in res:
+            res["saved"] = torch.empty((R, 8), dtype=torch.float32, device=dev)
+        if valid and "valid" not in res:
+            res["valid"] = torch.empty((R,), dtype=torch.uint8, device=dev)
+        if visits_cap > 0:
+            res.setdefault("visit_count", torch.empty((R,), dtype=torch.int32, device=dev))
+            res.setdefault("visits", torch.empty((R, visits_cap), dtype=torch.int32, device=dev))
+        o = L.Outputs()
+        for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits"):
+            if k in res:
+                setattr(o, k, res[k].data_ptr())
+        arr = (L.Actor * max(1, len(actors)))()
+        for k, (sc, p0, p1, base) in enumerate(actors):
+            arr[k].actor = sc._h
+            arr[k].pose0[:] = [float(v) for v in np.asarray(p0, dtype=np.float64).ravel()]
+            arr[k].pose1[:] = [float(v) for v in np.asarray(p1, dtype=np.float64).ravel()]
+            arr[k].id_base = int(base)
+        keep: list = [arr, [a[0] for a in actors]]
+        s = sensor_struct(sensor, keep)
+        op = opts_struct(t_min, background, want_intensity, visits_cap)
+        L.check(L.load().salf_render_rays_actors(self._h, arr, len(actors), C.byref(s),
+                                                 C.byref(op), C.byref(o), _stream_ptr(stream)),
+                "salf_render_rays_actors")
+        res["_keep"] = keep
+        return res
+
     def render_host(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
                     want_intensity=False, outputs=("rgb", "depth", "opacity"), out=None,
                     stream=None) -> dict:

@@ -60,6 +60,8 @@ extern "C" void salf_scene_destroy(salf_scene* s) {
   if (s->raster_pairs) cudaFree(s->raster_pairs);
   if (s->raster_count_host) cudaFreeHost(s->raster_count_host);
   if (s->raster_done) cudaEventDestroy(s->raster_done);
+  if (s->actor_buf) cudaFree(s->actor_buf);
+  if (s->actor_done) cudaEventDestroy(s->actor_done);
   delete s;
 }
 
@@ -192,6 +194,27 @@ static void mat_to_quat(const double* P, double q[4]) {
   for (int k = 0; k < 4; ++k) q[k] /= nn;
 }
 
+// Relative rotation R1 R0^T of two 3x4 poses as (world axis, angle), the
+// shortest way round: the slerp geodesic from R0 to R1 is
+// R(s) = rot(axis, s * angle) R0.
+void salf_relative_rotation(const double* pose0, const double* pose1, float axis[3],
+                            float* angle) {
+  double Rr[12] = {0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0;
+      for (int k = 0; k < 3; ++k) acc += pose1[4 * i + k] * pose0[4 * j + k];
+      Rr[4 * i + j] = acc;
+    }
+  double q[4];
+  mat_to_quat(Rr, q);
+  if (q[0] < 0)
+    for (int k = 0; k < 4; ++k) q[k] = -q[k];
+  const double vn = std::sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  *angle = vn > 0 ? (float)(2.0 * std::atan2(vn, q[0])) : 0.f;
+  for (int k = 0; k < 3; ++k) axis[k] = vn > 0 ? (float)(q[k + 1] / vn) : 0.f;
+}
+
 int salf_step_budget() {
   static const int budget = [] {
     const char* e = std::getenv("SALF_STEP_BUDGET");
@@ -284,23 +307,13 @@ salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* s,
   r->elev_step = s->height > 1 ? (float)(((double)s->elev_max - (double)s->elev_min) / (s->height - 1)) : 0.f;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) r->R0[3 * i + j] = (float)s->pose0[4 * i + j];
-  // relative rotation R1 R0^T as (world axis, angle), shortest way round: the
-  // slerp geodesic from R0 to R1 is R(s) = rot(axis, s * angle) R0
   {
-    double Rr[12] = {0};
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        double acc = 0;
-        for (int k = 0; k < 3; ++k) acc += s->pose1[4 * i + k] * s->pose0[4 * j + k];
-        Rr[4 * i + j] = acc;
-      }
-    double q[4];
-    mat_to_quat(Rr, q);
-    if (q[0] < 0)
-      for (int k = 0; k < 4; ++k) q[k] = -q[k];
-    const double vn = std::sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    r->rel_angle = vn > 0 ? (float)(2.0 * std::atan2(vn, q[0])) : 0.f;
-    for (int k = 0; k < 3; ++k) r->rel_axis[k] = vn > 0 ? (float)(q[k + 1] / vn) : 0.f;
+    double p0[12], p1[12];
+    for (int k = 0; k < 12; ++k) {
+      p0[k] = s->pose0[k];
+      p1[k] = s->pose1[k];
+    }
+    salf_relative_rotation(p0, p1, r->rel_axis, &r->rel_angle);
   }
   const bool timed = s->t1 > s->t0;
   r->moving = (s->kind == SALF_LIDAR_SPIN && timed) ||
@@ -514,6 +527,226 @@ extern "C" salf_status salf_render_raster(salf_scene* sc, const salf_sensor* sen
   r.vcount = out->visit_count;
   r.visits = out->visits;
   return salf_raster_run(sc, r, sen->fx, sen->fy, stats, static_cast<cudaStream_t>(stream));
+}
+
+// Oriented box: centre, unit axes (columns of the rotation), half extents.
+struct Obb {
+  double c[3], ax[3][3], h[3];
+};
+
+static Obb actor_obb(const salf_scene* a, const double* pose) {
+  Obb b;
+  double lo[3], hi[3], cl[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = a->origin[k] + a->dev.bmin[k] * a->sfin;
+    hi[k] = a->origin[k] + a->dev.bmax[k] * a->sfin;
+    cl[k] = 0.5 * (lo[k] + hi[k]);
+    b.h[k] = 0.5 * (hi[k] - lo[k]);
+  }
+  for (int i = 0; i < 3; ++i) {
+    b.c[i] = pose[4 * i + 3];
+    for (int j = 0; j < 3; ++j) {
+      b.c[i] += pose[4 * i + j] * cl[j];
+      b.ax[j][i] = pose[4 * i + j];  // axis j = column j of the rotation
+    }
+  }
+  return b;
+}
+
+// Separating-axis test of two oriented boxes (15 candidate axes); true if
+// their interiors overlap by more than `tol` along every axis.
+static bool obb_overlap(const Obb& A, const Obb& B, double tol) {
+  double d[3];
+  for (int k = 0; k < 3; ++k) d[k] = B.c[k] - A.c[k];
+  auto dot = [](const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
+  auto separated = [&](const double* L) {
+    const double n = std::sqrt(dot(L, L));
+    if (n < 1e-12) return false;  // degenerate (parallel edges): covered by the face axes
+    double ra = 0, rb = 0;
+    for (int k = 0; k < 3; ++k) {
+      ra += A.h[k] * std::fabs(dot(A.ax[k], L));
+      rb += B.h[k] * std::fabs(dot(B.ax[k], L));
+    }
+    return std::fabs(dot(d, L)) >= ra + rb - tol * n;
+  };
+  for (int k = 0; k < 3; ++k)
+    if (separated(A.ax[k]) || separated(B.ax[k])) return false;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double* u = A.ax[i];
+      const double* v = B.ax[j];
+      const double L[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2],
+                           u[0] * v[1] - u[1] * v[0]};
+      if (separated(L)) return false;
+    }
+  return true;
+}
+
+extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor* actors,
+                                              int32_t n_actors, const salf_sensor* sen,
+                                              const salf_render_opts* opts,
+                                              const salf_outputs* out, void* stream) {
+  if (!sc || !sen || !out || n_actors < 0 || (n_actors > 0 && !actors)) {
+    g_err = "salf_render_rays_actors: null argument or negative count";
+    return SALF_ERR_INVALID;
+  }
+  if (n_actors > SALF_MAX_ACTORS) {
+    g_err = "salf_render_rays_actors: more than SALF_MAX_ACTORS actors";
+    return SALF_ERR_INVALID;
+  }
+  const salf_render_opts o = opts ? *opts : default_opts();
+  if (out->on_host || out->ray_dump || out->steps) {
+    g_err = "salf_render_rays_actors: device outputs only (no ray_dump or steps)";
+    return SALF_ERR_INVALID;
+  }
+  if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
+      !(o.visits_cap > 0 && out->visits)) {
+    g_err = "salf_render_rays_actors: no output requested";
+    return SALF_ERR_INVALID;
+  }
+  if (o.visits_cap > 0 && (!out->visits || !out->visit_count)) {
+    g_err = "salf_render_rays_actors: visits_cap > 0 needs visits and visit_count";
+    return SALF_ERR_INVALID;
+  }
+  if (misaligned(out->saved, 16)) {
+    g_err = "salf_render_rays_actors: saved must be 16-byte aligned";
+    return SALF_ERR_INVALID;
+  }
+  for (int k = 0; k < n_actors; ++k) {
+    const salf_scene* a = actors[k].actor;
+    if (!a || a->device != sc->device || a->dtype != sc->dtype || a->mode != sc->mode) {
+      g_err = "salf_render_rays_actors: actor " + std::to_string(k) +
+              " is null or differs from the scene in device, dtype or field mode";
+      return SALF_ERR_INVALID;
+    }
+    for (int q = 0; q < 12; ++q)
+      if (!std::isfinite(actors[k].pose0[q]) || !std::isfinite(actors[k].pose1[q])) {
+        g_err = "salf_render_rays_actors: non-finite actor pose";
+        return SALF_ERR_INVALID;
+      }
+  }
+  // actor boxes pairwise disjoint at t0 and at t1
+  for (int i = 0; i < n_actors; ++i) {
+    if (actors[i].actor->n == 0) continue;
+    for (int j = i + 1; j < n_actors; ++j) {
+      if (actors[j].actor->n == 0) continue;
+      for (int t = 0; t < 2; ++t) {
+        const double* pi = t ? actors[i].pose1 : actors[i].pose0;
+        const double* pj = t ? actors[j].pose1 : actors[j].pose0;
+        if (obb_overlap(actor_obb(actors[i].actor, pi), actor_obb(actors[j].actor, pj), 1e-9)) {
+          g_err = "salf_render_rays_actors: boxes of actors " + std::to_string(i) + " and " +
+                  std::to_string(j) + " overlap at t" + std::to_string(t);
+          return SALF_ERR_OVERLAP;
+        }
+      }
+    }
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  LaunchParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.S = sc->dev;
+  P.n_req = 1;
+  ReqDev& r = P.req[0];
+  salf_status st = salf_prepare_request(sc, sen, &o, &r);
+  if (st != SALF_OK) return st;
+  P.total_tiles = r.n_tiles;
+  P.step_budget = salf_step_budget();
+  r.rgb = out->rgb;
+  r.depth = out->depth;
+  r.opacity = out->opacity;
+  r.intensity = out->intensity;
+  r.saved = out->saved;
+  r.valid = out->valid;
+  r.vcount = out->visit_count;
+  r.visits = out->visits;
+
+  // per-actor constants (FP64 -> FP32)
+  std::vector<ActorDev> ad;
+  ad.reserve((size_t)n_actors);
+  double os0[3], os1[3];
+  for (int a = 0; a < 3; ++a) {
+    os0[a] = sen->pose0[4 * a + 3];
+    os1[a] = r.moving ? sen->pose1[4 * a + 3] : os0[a];
+  }
+  for (int k = 0; k < n_actors; ++k) {
+    const salf_scene* as = actors[k].actor;
+    if (as->n == 0) continue;
+    ActorDev A;
+    std::memset(&A, 0, sizeof(A));
+    A.S = as->dev;
+    const double* p0 = actors[k].pose0;
+    const double* p1 = actors[k].pose1;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A.R0[3 * i + j] = (float)p0[4 * i + j];
+    salf_relative_rotation(p0, p1, A.axis, &A.angle);
+    double lo[3], hi[3], cl[3], h2 = 0, cn2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      A.orel0[a] = (float)(os0[a] - p0[4 * a + 3]);
+      A.orel1[a] = (float)(os1[a] - p1[4 * a + 3]);
+      lo[a] = as->origin[a] + as->dev.bmin[a] * as->sfin;
+      hi[a] = as->origin[a] + as->dev.bmax[a] * as->sfin;
+      A.box_lo[a] = (float)lo[a];
+      A.box_hi[a] = (float)hi[a];
+      A.origin[a] = (float)as->origin[a];
+      cl[a] = 0.5 * (lo[a] + hi[a]);
+      h2 += 0.25 * (hi[a] - lo[a]) * (hi[a] - lo[a]);
+      cn2 += cl[a] * cl[a];
+    }
+    A.inv_sfin = (float)(1.0 / as->sfin);
+    double c0n2 = 0;
+    for (int i = 0; i < 3; ++i) {
+      double w0 = p0[4 * i + 3] - os0[i], w1 = p1[4 * i + 3] - os1[i];
+      for (int j = 0; j < 3; ++j) {
+        w0 += p0[4 * i + j] * cl[j];
+        w1 += p1[4 * i + j] * cl[j];
+      }
+      A.cc0[i] = (float)w0;
+      A.cc1[i] = (float)w1;
+      c0n2 += w0 * w0;
+    }
+    // the centre follows an arc between its end positions: its chord is off by
+    // at most |c| (1 - cos(angle / 2)) <= |c| angle^2 / 8
+    const double ang = std::fabs((double)A.angle);
+    A.radius = (float)(std::sqrt(h2) + std::sqrt(cn2) * ang * ang / 8.0 +
+                       1e-3 * (1.0 + std::sqrt(c0n2)));
+    A.id_base = actors[k].id_base;
+    ad.push_back(A);
+  }
+  const int na = (int)ad.size();
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(sc->actor_mu);
+  if (!sc->actor_done) {
+    if ((e = cudaEventCreateWithFlags(&sc->actor_done, cudaEventDisableTiming)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor event");
+  } else if ((e = cudaStreamWaitEvent(cs, sc->actor_done, 0)) != cudaSuccess) {
+    return salf_cuda_fail(e, "actor event wait");
+  }
+  const size_t bytes = std::max<size_t>(1, (size_t)na) * sizeof(ActorDev);
+  if (sc->actor_buf_bytes < bytes) {
+    if ((e = cudaEventSynchronize(sc->actor_done)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor sync");
+    if (sc->actor_buf) cudaFree(sc->actor_buf);
+    sc->actor_buf = nullptr;
+    sc->actor_buf_bytes = 0;
+    const size_t grow = std::max<size_t>(bytes, 16 * sizeof(ActorDev));
+    if (cudaMalloc(&sc->actor_buf, grow) != cudaSuccess) {
+      cudaGetLastError();
+      g_err = "salf_render_rays_actors: out of device memory";
+      return SALF_ERR_OOM;
+    }
+    sc->actor_buf_bytes = grow;
+  }
+  ActorDev* dact = static_cast<ActorDev*>(sc->actor_buf);
+  if (na > 0 &&
+      (e = cudaMemcpyAsync(dact, ad.data(), (size_t)na * sizeof(ActorDev), cudaMemcpyHostToDevice,
+                           cs)) != cudaSuccess)
+    return salf_cuda_fail(e, "actor table upload");
+  if ((e = salf_launch_actors(P, dact, na, cs)) != cudaSuccess)
+    return salf_cuda_fail(e, "actor launch");
+  if ((e = cudaEventRecord(sc->actor_done, cs)) != cudaSuccess)
+    return salf_cuda_fail(e, "actor event");
+  return SALF_OK;
 }
 
 extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* sen,

@@ -23,6 +23,7 @@
 // Device status-word bits.
 #define SALF_DEVERR_STEP_CAP 1  // a traversal loop reached its iteration bound
 #define SALF_DEVERR_SDF_AB 2    // an SDF record has a <= 0 or b <= 0
+#define SALF_DEVERR_ACTOR_CAP 4 // a ray met more actor boxes than it can hold
 
 // Read-only view of a built scene, passed to kernels by value.
 //
@@ -122,6 +123,22 @@ struct ReqDev {
   float* d_params;
 };
 
+// One placed actor as the actor kernel sees it (prepared on the host in FP64
+// for one request; frames: world = the static scene's, canonical = the
+// actor scene's).
+struct ActorDev {
+  DevScene S;           // the actor's voxels (canonical frame)
+  float R0[9];          // canonical -> world rotation at the sensor's t0
+  float axis[3], angle; // R(s) = rot(axis, s * angle) R0
+  float orel0[3], orel1[3];  // sensor origin minus actor position at t0, t1 (world m)
+  float cc0[3], cc1[3];      // bounding-sphere centre minus sensor origin at t0, t1
+  float radius;
+  float origin[3];      // actor grid min corner (canonical m)
+  float inv_sfin;       // actor finest cells per metre
+  float box_lo[3], box_hi[3];  // tight box of the actor's voxels (canonical m)
+  int id_base;          // visit ids of its voxels: id_base + input index
+};
+
 struct LaunchParams {
   DevScene S;
   int n_req;
@@ -160,6 +177,11 @@ struct salf_scene {
   size_t raster_pairs_bytes = 0;
   unsigned long long* raster_count_host = nullptr;
   cudaEvent_t raster_done = nullptr;  // end of the last call's GPU work
+  // per-call actor tables (grown on demand, guarded by actor_mu)
+  std::mutex actor_mu;
+  void* actor_buf = nullptr;
+  size_t actor_buf_bytes = 0;
+  cudaEvent_t actor_done = nullptr;
 };
 
 // Implemented in the .cu / .cpp files of the library.
@@ -169,12 +191,16 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
 salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* sen,
                                  const salf_render_opts* opts, ReqDev* r);
 int64_t salf_request_rays(const salf_sensor* sen);
+void salf_relative_rotation(const double* pose0, const double* pose1, float axis[3],
+                            float* angle);
 // Structure steps per lane between warp-wide compositing rounds (environment
 // override SALF_STEP_BUDGET, read once).
 int salf_step_budget();
 cudaError_t salf_launch_gather_params(const float* in, const int* order, void* out, int64_t n,
                                       int dtype, int mode, int* status, cudaStream_t st);
 cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st);
+cudaError_t salf_launch_actors(const LaunchParams& P, const ActorDev* actors, int n_actors,
+                               cudaStream_t st);
 // Tile rasterisation of one pinhole request (r prepared by
 // salf_prepare_request, outputs set); fills *stats when non-null.
 salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double fy,
