@@ -8,9 +8,9 @@
 //     (a bounding-sphere test, then a slab test against the actor's tight box
 //     in its frame);
 //  2. the static walk and one actor walk at a time (actor boxes are disjoint,
-//     so their intervals are too) advance together; the hit with the smaller
-//     entry is composited first (the static one on ties), by Eq. 3-4 with
-//     early termination;
+//     so their intervals are too) advance together, one structure step per
+//     lane per warp-wide round; the hit with the smaller entry is composited
+//     first (the static one on ties), by Eq. 3-4 with early termination;
 //  3. an actor hit's field uses the ray moved into the actor's frame: local
 //     coordinates and the SH view direction of the canonical frame.
 // A rigid map keeps distances along the ray, so both walks' t are metres
@@ -27,8 +27,13 @@ using namespace salf;
 
 namespace {
 
+#ifndef SALF_ACTOR_MIN_BLOCKS
+#define SALF_ACTOR_MIN_BLOCKS 1  // resident merge blocks per SM the register budget must allow
+#endif
+
 constexpr int kActorWarps = 4;  // warps per block
 constexpr int kMaxIntervals = 8;
+constexpr int kMaskWords = SALF_MAX_ACTORS / 32;  // per-tile candidate actors (bits)
 
 __device__ __forceinline__ void rotate_about(const float k[3], float sa, float omc, float v[3]) {
   // Rodrigues: v + sin(a) (k x v) + (1 - cos(a)) k x (k x v)
@@ -65,6 +70,134 @@ __device__ __forceinline__ void actor_frame(const ActorDev& A, float s, const fl
   }
 }
 
+// Conservative test: may the ray (direction d from the sensor origin at time
+// fraction s, over [tn, tf]) meet actor A's box?  Its bounding sphere.
+__device__ __forceinline__ bool may_meet(const ActorDev& A, const Ray& r) {
+  float c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) c[a] = fmaf(r.s, A.cc1[a] - A.cc0[a], A.cc0[a]);
+  const float tca = c[0] * r.d[0] + c[1] * r.d[1] + c[2] * r.d[2];
+  const float d2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2] - tca * tca;
+  return !(d2 > A.radius * A.radius || tca + A.radius < r.tn || tca - A.radius > r.tf);
+}
+
+// Exact test: the ray's [t_in, t_out] with actor A's tight box (in its frame),
+// clipped to the ray's [tn, tf]; false if empty.
+__device__ __forceinline__ bool box_interval(const ActorDev& A, const Ray& r, float* t_in) {
+  float oc[3], dc[3];
+  actor_frame(A, r.s, r.d, oc, dc);
+  float a0 = r.tn, a1 = r.tf;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float inv = 1.f / (fabsf(dc[a]) < 1e-20f ? 1e-20f : dc[a]);
+    const float p = (A.box_lo[a] - oc[a]) * inv, q = (A.box_hi[a] - oc[a]) * inv;
+    a0 = fmaxf(a0, fminf(p, q));
+    a1 = fminf(a1, fmaxf(p, q));
+  }
+  *t_in = a0;
+  return a1 > a0;
+}
+
+// Split the request's tiles into those whose rays may meet an actor (list 1,
+// rendered by the merge kernel) and the rest (list 0, rendered by the plain
+// ray kernel).  One warp per tile, tiles taken in launch order.
+__global__ void __launch_bounds__(128) k_classify_tiles(const __grid_constant__ LaunchParams P,
+                                                        const ActorDev* __restrict__ actors,
+                                                        int n_actors, int* __restrict__ lists,
+                                                        int* __restrict__ counts,
+                                                        unsigned* __restrict__ masks) {
+  const int tile = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (tile >= P.req[0].n_tiles) return;
+  const int lane = threadIdx.x & 31;
+  const ReqDev& Q = P.req[0];
+  int u0, v0;
+  tile_origin(Q, tile, &u0, &v0);
+  const int u = u0 + lane % Q.tile_w, v = v0 + lane / Q.tile_w;
+  // the warp's rays as a cone: mean direction, cosine of the widest ray, the
+  // range of time fractions and of t_near / t_far
+  Ray r;
+  r.s = 0.f;
+  r.valid = false;
+  r.d[0] = r.d[1] = r.d[2] = 0.f;
+  r.tn = 0.f;
+  r.tf = 0.f;
+  const bool in_img = u < Q.W && v < Q.H;
+  if (in_img) gen_ray(Q, P.S, u, v, v * Q.W + u, r);
+  const bool ok = in_img && r.valid;
+  float m[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float x = ok ? r.d[a] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    m[a] = x;
+  }
+  const float mn = sqrtf(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  bool any = false;
+  if (__any_sync(0xffffffffu, ok) && mn > 0.f) {
+    const float inv = 1.f / mn;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) m[a] *= inv;
+    float cmin = ok ? m[0] * r.d[0] + m[1] * r.d[1] + m[2] * r.d[2] : 1.f;
+    float smin = ok ? r.s : 1.f, smax = ok ? r.s : 0.f, tn = ok ? r.tn : 3.4e38f, tf = ok ? r.tf : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+      smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+      smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+      tn = fminf(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+      tf = fmaxf(tf, __shfl_xor_sync(0xffffffffu, tf, o));
+    }
+    // widen by FP32 slack; a cone wider than 90 degrees accepts everything
+    const float half = acosf(fminf(fmaxf(cmin, -1.f), 1.f)) + 1e-4f;
+    // each lane tests actors lane, lane + 32, ...: the sphere (centre moving
+    // linearly over [smin, smax]: its segment's bounding sphere) against the cone
+    for (int k0 = 0; k0 < n_actors; k0 += 32) {
+      const int k = k0 + lane;
+      bool meet = false;
+      if (k < n_actors) {
+      const ActorDev& A = actors[k];
+      float c0[3], c1[3], c[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        c0[a] = fmaf(smin, A.cc1[a] - A.cc0[a], A.cc0[a]);
+        c1[a] = fmaf(smax, A.cc1[a] - A.cc0[a], A.cc0[a]);
+        c[a] = 0.5f * (c0[a] + c1[a]);
+      }
+      const float dx = c1[0] - c0[0], dy = c1[1] - c0[1], dz = c1[2] - c0[2];
+      const float rad = A.radius + 0.5f * sqrtf(dx * dx + dy * dy + dz * dz);
+      const float dist = sqrtf(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+      if (dist <= rad) {
+        meet = true;  // the sensor is inside the sphere
+      } else if (half >= 1.5707963f) {
+        meet = true;
+      } else {
+        // angle between the cone axis and the centre, less the sphere's angular radius
+        const float ca = fminf(fmaxf((m[0] * c[0] + m[1] * c[1] + m[2] * c[2]) / dist, -1.f), 1.f);
+        const float ang = acosf(ca) - asinf(fminf(rad / dist, 1.f));
+        meet = ang <= half && dist - rad <= tf && dist + rad >= tn;
+      }
+      }
+      // the cone's candidates, then each lane's own ray against each candidate box
+      unsigned cand = __ballot_sync(0xffffffffu, meet), hit = 0u;
+      while (cand) {
+        const int j = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        float tin;
+        const bool mine = ok && may_meet(actors[k0 + j], r) && box_interval(actors[k0 + j], r, &tin);
+        if (__any_sync(0xffffffffu, mine)) hit |= 1u << j;
+      }
+      if (lane == 0) masks[(size_t)tile * kMaskWords + (k0 >> 5)] = hit;
+      any = any || hit != 0u;
+    }
+  }
+  if (lane == 0) {
+    const int which = any ? 1 : 0;
+    const int slot = atomicAdd(&counts[which], 1);
+    lists[which * Q.n_tiles + slot] = tile;
+  }
+}
+
 // Start actor A's walk for the ray (frame conversion to its grid cells).
 __device__ __forceinline__ void actor_walk(const ActorDev& A, const Ray& r, Walk& w,
                                            float gam[4]) {
@@ -88,15 +221,21 @@ __device__ __forceinline__ void actor_walk(const ActorDev& A, const Ray& r, Walk
 }
 
 template <int DT, int MODE, bool DUMP>
-__global__ void __launch_bounds__(32 * kActorWarps) k_forward_actors(
-    const __grid_constant__ LaunchParams P, const ActorDev* __restrict__ actors, int n_actors) {
+__global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_forward_actors(
+    const __grid_constant__ LaunchParams P, const ActorDev* __restrict__ actors, int n_actors,
+    const unsigned* __restrict__ masks) {
   const int warp = blockIdx.x * kActorWarps + (threadIdx.x >> 5);
   if (warp >= P.total_tiles) return;
   const int lane = threadIdx.x & 31;
   const ReqDev& Q = P.req[0];
   const DevScene& S = P.S;
+  int tile = warp - Q.tile_begin;
+  if (Q.tile_list) {
+    if (tile >= __ldg(Q.tile_count)) return;
+    tile = __ldg(&Q.tile_list[tile]);
+  }
   int u0, v0;
-  tile_origin(Q, warp - Q.tile_begin, &u0, &v0);
+  tile_origin(Q, tile, &u0, &v0);
   const int u = u0 + lane % Q.tile_w;
   const int v = v0 + lane / Q.tile_w;
   const bool in_img = (u < Q.W) && (v < Q.H);
@@ -120,47 +259,41 @@ __global__ void __launch_bounds__(32 * kActorWarps) k_forward_actors(
   int iv_k[kMaxIntervals];
   int ni = 0;
   if (in_img && r.valid) {
-    const float tf = r.tf;
-    for (int k = 0; k < n_actors; ++k) {
-      const ActorDev& A = actors[k];
-      float c[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) c[a] = fmaf(r.s, A.cc1[a] - A.cc0[a], A.cc0[a]);
-      const float tca = c[0] * r.d[0] + c[1] * r.d[1] + c[2] * r.d[2];
-      const float d2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2] - tca * tca;
-      if (d2 > A.radius * A.radius || tca + A.radius < r.tn || tca - A.radius > tf) continue;
-      float oc[3], dc[3];
-      actor_frame(A, r.s, r.d, oc, dc);
-      float a0 = r.tn, a1 = tf;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float inv = 1.f / (fabsf(dc[a]) < 1e-20f ? 1e-20f : dc[a]);
-        const float p = (A.box_lo[a] - oc[a]) * inv, q = (A.box_hi[a] - oc[a]) * inv;
-        a0 = fmaxf(a0, fminf(p, q));
-        a1 = fminf(a1, fmaxf(p, q));
+    // candidates: the actors the tile's cone may meet
+    for (int wd = 0; wd * 32 < n_actors; ++wd) {
+      unsigned bits = __ldg(&masks[(size_t)tile * kMaskWords + wd]);
+      while (bits) {
+        const int k = wd * 32 + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const ActorDev& A = actors[k];
+        float a0;
+        if (!may_meet(A, r) || !box_interval(A, r, &a0)) continue;
+        // insertion into the sorted list (the farthest is dropped when full)
+        int pos = ni < kMaxIntervals ? ni : kMaxIntervals - 1;
+        if (ni == kMaxIntervals) {
+          atomicOr(S.status, SALF_DEVERR_ACTOR_CAP);
+          if (a0 >= iv_in[pos]) continue;
+        } else {
+          ++ni;
+        }
+        while (pos > 0 && iv_in[pos - 1] > a0) {
+          iv_in[pos] = iv_in[pos - 1];
+          iv_k[pos] = iv_k[pos - 1];
+          --pos;
+        }
+        iv_in[pos] = a0;
+        iv_k[pos] = k;
       }
-      if (!(a1 > a0)) continue;
-      // insertion into the sorted list (the farthest is dropped when full)
-      int pos = ni < kMaxIntervals ? ni : kMaxIntervals - 1;
-      if (ni == kMaxIntervals) {
-        atomicOr(S.status, SALF_DEVERR_ACTOR_CAP);
-        if (a0 >= iv_in[pos]) continue;
-      } else {
-        ++ni;
-      }
-      while (pos > 0 && iv_in[pos - 1] > a0) {
-        iv_in[pos] = iv_in[pos - 1];
-        iv_k[pos] = iv_k[pos - 1];
-        --pos;
-      }
-      iv_in[pos] = a0;
-      iv_k[pos] = k;
     }
   }
 
-  // 2. merge the static walk with one actor walk at a time
+  // 2. merge the static walk with one actor walk at a time, in warp-wide
+  // rounds: per round a lane takes at most one structure step (of the static
+  // or the actor walk), then composites the next hit once both walks have
+  // resolved theirs
   const bool want_int = Q.want_int != 0;
   const float tmin = Q.t_min;
+  const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   Accum acc{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
   Hit hs, ha;
   bool hs_ok = false, ha_ok = false;
@@ -168,25 +301,28 @@ __global__ void __launch_bounds__(32 * kActorWarps) k_forward_actors(
   wa.alive = false;
   float gam_a[4] = {0.f, 0.f, 0.f, 0.f};
   int cur = -1, nxt = 0;
-  const int unlimited = 1 << 30;
-  bool done = !(in_img && r.valid);
-  while (!done) {
-    if (!hs_ok && ws.alive) hs_ok = next_hit(S, ws, hs, unlimited);
-    // an actor whose box the ray enters before the pending static hit starts
-    // now (a little early is harmless: the merge orders hits by entry)
-    if (cur < 0 && nxt < ni &&
-        (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)))) {
+  bool live = in_img && r.valid;
+  for (;;) {
+    if (!__any_sync(0xffffffffu, live)) break;
+    if (!live) continue;
+    if (cur >= 0 && !ha_ok && !wa.alive) cur = -1;  // the open actor is exhausted
+    // the next actor box starts before the pending static hit (a little early
+    // is harmless: hits are composited by entry)
+    const bool start_next =
+        cur < 0 && nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)));
+    if (!hs_ok && ws.alive) {
+      hs_ok = next_hit(S, ws, hs, budget);
+    } else if (start_next) {
       cur = iv_k[nxt++];
       actor_walk(actors[cur], r, wa, gam_a);
       ha_ok = false;
+    } else if (cur >= 0 && !ha_ok && wa.alive) {
+      ha_ok = next_hit(actors[cur].S, wa, ha, budget);
     }
-    if (cur >= 0 && !ha_ok) {
-      if (wa.alive) ha_ok = next_hit(actors[cur].S, wa, ha, unlimited);
-      if (!ha_ok && !wa.alive) {
-        cur = -1;
-        continue;
-      }
-    }
+    const bool s_res = hs_ok || !ws.alive;
+    const bool a_res = cur < 0 ? !(nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin))))
+                               : (ha_ok || !wa.alive);
+    if (!(s_res && a_res)) continue;
     if (ha_ok && (!hs_ok || ha.tin < hs.tin)) {
       const ActorDev& A = actors[cur];
       const GlobalRec src{reinterpret_cast<const float4*>(A.S.params) +
@@ -203,12 +339,12 @@ __global__ void __launch_bounds__(32 * kActorWarps) k_forward_actors(
         Q.visits[(size_t)ray * Q.vcap + acc.nvis] = __ldg(&S.order[hs.vox]);
       hs_ok = false;
     } else {
-      // nothing pending: finished unless an actor is still to start
-      if (cur < 0 && nxt >= ni && !ws.alive) break;
+      // both walks exhausted and no actor left to open
+      if (cur < 0 && nxt >= ni) live = false;
       continue;
     }
     ++acc.nvis;
-    if (acc.T < tmin) done = true;
+    if (acc.T < tmin) live = false;
   }
   if (!in_img) return;
   write_outputs(Q, ray, r.valid, acc);
@@ -219,29 +355,37 @@ __global__ void __launch_bounds__(32 * kActorWarps) k_forward_actors(
 }
 
 template <int DT, int MODE>
-void launch_actors(const LaunchParams& P, const ActorDev* actors, int n, bool dump,
-                   cudaStream_t st) {
+void launch_actors(const LaunchParams& P, const ActorDev* actors, int n, const unsigned* masks,
+                   bool dump, cudaStream_t st) {
   const int blocks = (P.total_tiles + kActorWarps - 1) / kActorWarps;
   if (blocks == 0) return;
   if (dump)
-    k_forward_actors<DT, MODE, true><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n);
+    k_forward_actors<DT, MODE, true><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n, masks);
   else
-    k_forward_actors<DT, MODE, false><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n);
+    k_forward_actors<DT, MODE, false><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n, masks);
 }
 
 }  // namespace
 
+cudaError_t salf_launch_classify(const LaunchParams& P, const ActorDev* actors, int n_actors,
+                                 int* lists, int* counts, unsigned* masks, cudaStream_t st) {
+  const int blocks = (P.req[0].n_tiles + 3) / 4;
+  if (blocks > 0)
+    k_classify_tiles<<<blocks, 128, 0, st>>>(P, actors, n_actors, lists, counts, masks);
+  return cudaGetLastError();
+}
+
 cudaError_t salf_launch_actors(const LaunchParams& P, const ActorDev* actors, int n_actors,
-                               cudaStream_t st) {
+                               const unsigned* masks, cudaStream_t st) {
   const bool dump = P.req[0].vcap > 0;
   const int dt = P.S.dtype, md = P.S.mode;
   if (dt == SALF_F32 && md == SALF_FIELD_EXP)
-    launch_actors<SALF_F32, SALF_FIELD_EXP>(P, actors, n_actors, dump, st);
+    launch_actors<SALF_F32, SALF_FIELD_EXP>(P, actors, n_actors, masks, dump, st);
   else if (dt == SALF_F32)
-    launch_actors<SALF_F32, SALF_FIELD_SDF>(P, actors, n_actors, dump, st);
+    launch_actors<SALF_F32, SALF_FIELD_SDF>(P, actors, n_actors, masks, dump, st);
   else if (md == SALF_FIELD_EXP)
-    launch_actors<SALF_BF16, SALF_FIELD_EXP>(P, actors, n_actors, dump, st);
+    launch_actors<SALF_BF16, SALF_FIELD_EXP>(P, actors, n_actors, masks, dump, st);
   else
-    launch_actors<SALF_BF16, SALF_FIELD_SDF>(P, actors, n_actors, dump, st);
+    launch_actors<SALF_BF16, SALF_FIELD_SDF>(P, actors, n_actors, masks, dump, st);
   return cudaGetLastError();
 }

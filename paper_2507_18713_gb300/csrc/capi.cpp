@@ -62,6 +62,9 @@ extern "C" void salf_scene_destroy(salf_scene* s) {
   if (s->raster_done) cudaEventDestroy(s->raster_done);
   if (s->actor_buf) cudaFree(s->actor_buf);
   if (s->actor_done) cudaEventDestroy(s->actor_done);
+  if (s->actor_fork) cudaEventDestroy(s->actor_fork);
+  if (s->actor_join) cudaEventDestroy(s->actor_join);
+  if (s->actor_aux) cudaStreamDestroy(s->actor_aux);
   delete s;
 }
 
@@ -722,14 +725,16 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
   } else if ((e = cudaStreamWaitEvent(cs, sc->actor_done, 0)) != cudaSuccess) {
     return salf_cuda_fail(e, "actor event wait");
   }
-  const size_t bytes = std::max<size_t>(1, (size_t)na) * sizeof(ActorDev);
+  const size_t table_bytes = ((std::max<size_t>(1, (size_t)na) * sizeof(ActorDev)) + 255) & ~(size_t)255;
+  const size_t mask_bytes = (size_t)r.n_tiles * (SALF_MAX_ACTORS / 32) * sizeof(unsigned);
+  const size_t bytes = table_bytes + mask_bytes + (2 * (size_t)r.n_tiles + 2) * sizeof(int);
   if (sc->actor_buf_bytes < bytes) {
     if ((e = cudaEventSynchronize(sc->actor_done)) != cudaSuccess)
       return salf_cuda_fail(e, "actor sync");
     if (sc->actor_buf) cudaFree(sc->actor_buf);
     sc->actor_buf = nullptr;
     sc->actor_buf_bytes = 0;
-    const size_t grow = std::max<size_t>(bytes, 16 * sizeof(ActorDev));
+    const size_t grow = bytes + bytes / 4;
     if (cudaMalloc(&sc->actor_buf, grow) != cudaSuccess) {
       cudaGetLastError();
       g_err = "salf_render_rays_actors: out of device memory";
@@ -738,12 +743,47 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
     sc->actor_buf_bytes = grow;
   }
   ActorDev* dact = static_cast<ActorDev*>(sc->actor_buf);
-  if (na > 0 &&
-      (e = cudaMemcpyAsync(dact, ad.data(), (size_t)na * sizeof(ActorDev), cudaMemcpyHostToDevice,
-                           cs)) != cudaSuccess)
-    return salf_cuda_fail(e, "actor table upload");
-  if ((e = salf_launch_actors(P, dact, na, cs)) != cudaSuccess)
-    return salf_cuda_fail(e, "actor launch");
+  unsigned* masks = reinterpret_cast<unsigned*>(static_cast<char*>(sc->actor_buf) + table_bytes);
+  int* lists = reinterpret_cast<int*>(static_cast<char*>(sc->actor_buf) + table_bytes + mask_bytes);
+  int* counts = lists + 2 * (size_t)r.n_tiles;
+  if (na == 0) {
+    // no actor in the request: the plain ray kernel
+    if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
+  } else {
+    if ((e = cudaMemcpyAsync(dact, ad.data(), (size_t)na * sizeof(ActorDev),
+                             cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor table upload");
+    if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), cs)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor tile counts");
+    // tiles whose rays may meet an actor go to the merge kernel, the rest to
+    // the plain ray kernel
+    if ((e = salf_launch_classify(P, dact, na, lists, counts, masks, cs)) != cudaSuccess)
+      return salf_cuda_fail(e, "tile classification");
+    // the two tile sets are disjoint: the merge kernel runs on an auxiliary
+    // stream beside the ray kernel (fork after the classification, join
+    // before the call's end event)
+    if (!sc->actor_aux) {
+      if ((e = cudaStreamCreateWithFlags(&sc->actor_aux, cudaStreamNonBlocking)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&sc->actor_fork, cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&sc->actor_join, cudaEventDisableTiming)) != cudaSuccess)
+        return salf_cuda_fail(e, "actor stream");
+    }
+    if ((e = cudaEventRecord(sc->actor_fork, cs)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(sc->actor_aux, sc->actor_fork, 0)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor fork");
+    LaunchParams Pa = P;
+    Pa.req[0].tile_list = lists + r.n_tiles;
+    Pa.req[0].tile_count = counts + 1;
+    if ((e = salf_launch_actors(Pa, dact, na, masks, sc->actor_aux)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor launch");
+    LaunchParams Ps = P;
+    Ps.req[0].tile_list = lists;
+    Ps.req[0].tile_count = counts;
+    if ((e = salf_launch_forward(Ps, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
+    if ((e = cudaEventRecord(sc->actor_join, sc->actor_aux)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(cs, sc->actor_join, 0)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor join");
+  }
   if ((e = cudaEventRecord(sc->actor_done, cs)) != cudaSuccess)
     return salf_cuda_fail(e, "actor event");
   return SALF_OK;

@@ -44,8 +44,13 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   const int lane = threadIdx.x & 31;
   const ReqDev& Q = P.req[find_request(P, warp)];
   const DevScene& S = P.S;
+  int tile = warp - Q.tile_begin;
+  if (Q.tile_list) {
+    if (tile >= __ldg(Q.tile_count)) return;
+    tile = __ldg(&Q.tile_list[tile]);
+  }
   int u0, v0;
-  tile_origin(Q, warp - Q.tile_begin, &u0, &v0);
+  tile_origin(Q, tile, &u0, &v0);
   const int u = u0 + lane % Q.tile_w;
   const int v = v0 + lane / Q.tile_w;
   const bool in_img = (u < Q.W) && (v < Q.H);

@@ -114,6 +114,10 @@ struct ReqDev {
   int tile_w, tile_h;
   int tile_begin, n_tiles;
   int first_row;
+  // optional subset of the tiles (device): warp w of the request renders
+  // tile tile_list[w] while w < *tile_count (null: every tile, in order)
+  const int* tile_list;
+  const int* tile_count;
   // backward inputs (unused by the forward kernel)
   const float* bsaved;
   const float* g_rgb;
@@ -182,6 +186,9 @@ struct salf_scene {
   void* actor_buf = nullptr;
   size_t actor_buf_bytes = 0;
   cudaEvent_t actor_done = nullptr;
+  // the merge kernel runs on this stream beside the ray kernel (fork / join)
+  cudaStream_t actor_aux = nullptr;
+  cudaEvent_t actor_fork = nullptr, actor_join = nullptr;
 };
 
 // Implemented in the .cu / .cpp files of the library.
@@ -199,8 +206,14 @@ int salf_step_budget();
 cudaError_t salf_launch_gather_params(const float* in, const int* order, void* out, int64_t n,
                                       int dtype, int mode, int* status, cudaStream_t st);
 cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st);
+// masks: per tile, SALF_MAX_ACTORS / 32 words of candidate actors (bits).
 cudaError_t salf_launch_actors(const LaunchParams& P, const ActorDev* actors, int n_actors,
-                               cudaStream_t st);
+                               const unsigned* masks, cudaStream_t st);
+// Tiles of request 0 whose rays may meet an actor -> lists[n_tiles + i],
+// the others -> lists[i]; counts[1], counts[0] (zeroed by the caller); per
+// tile the candidate actors -> masks.
+cudaError_t salf_launch_classify(const LaunchParams& P, const ActorDev* actors, int n_actors,
+                                 int* lists, int* counts, unsigned* masks, cudaStream_t st);
 // Tile rasterisation of one pinhole request (r prepared by
 // salf_prepare_request, outputs set); fills *stats when non-null.
 salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double fy,
