@@ -12,6 +12,8 @@ from .oracle import (  # noqa: F401
     library_path,
     render,
     render_actors,
+    refine,
+    subdivide_record,
     backward,
     gen_rays,
     trace,

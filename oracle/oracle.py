@@ -60,7 +60,7 @@ class _Outputs(C.Structure):
     _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("opacity", C.c_void_p),
                 ("intensity", C.c_void_p), ("t_end", C.c_void_p), ("term_gap", C.c_void_p),
                 ("n_visits", C.c_void_p), ("valid", C.c_void_p), ("visits", C.c_void_p),
-                ("visits_cap", C.c_int32)]
+                ("visits_cap", C.c_int32), ("max_alpha", C.c_void_p)]
 
 
 class _Actor(C.Structure):
@@ -97,6 +97,7 @@ def _load():
             lib.orc_backward.argtypes = [vp, C.POINTER(_Sensor), C.POINTER(_Opts), vp, i64, vp,
                                          vp, vp, vp, vp]
             lib.orc_num_threads.restype = C.c_int
+            lib.orc_subdivide_record.argtypes = [vp, i32, vp]
             lib.orc_render_actors.argtypes = [vp, vp, i32, C.POINTER(_Sensor), C.POINTER(_Opts),
                                               vp, i64, C.POINTER(_Outputs)]
             _lib = lib
@@ -259,8 +260,10 @@ def trace_eps(oscene, o, d, t_near, t_far, eps_abs, eps_rel, sign, cap=1 << 16,
 
 
 def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
-           want_intensity=False, brute_force=False, visits_cap=0):
-    """Render the selected rays (all if idx is None) in FP64."""
+           want_intensity=False, brute_force=False, visits_cap=0, max_alpha=None):
+    """Render the selected rays (all if idx is None) in FP64.  `max_alpha`
+    (n float64, input order) is max-accumulated with each voxel's largest
+    composited alpha."""
     lib = _load()
     s, keep = _sensor(sensor)
     idx, m = _idx(sensor, idx)
@@ -274,6 +277,9 @@ def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
         res["visits"] = np.full((m, visits_cap), -1, np.int32)
         o.visits = _ptr(res["visits"])
         o.visits_cap = int(visits_cap)
+    if max_alpha is not None:
+        assert max_alpha.dtype == np.float64 and max_alpha.flags.c_contiguous
+        o.max_alpha = _ptr(max_alpha)
     opt = _opts(t_min, background, want_intensity, brute_force)
     st = lib.orc_render(oscene._h, C.byref(s), C.byref(opt), _ptr(idx), m, C.byref(o))
     if st != 0:
@@ -339,3 +345,40 @@ def render_actors(oscene, actors, sensor, idx=None, t_min=1e-4, background=(0.0,
     del keep
     res["valid"] = res["valid"].astype(bool)
     return res
+
+
+def subdivide_record(record, child):
+    """Record of child `child` (0..7) of a voxel split in 8 (Sec. III-C)."""
+    rec = np.ascontiguousarray(record, dtype=np.float64)
+    out = np.zeros(32)
+    _load().orc_subdivide_record(_ptr(rec), int(child), _ptr(out))
+    return out
+
+
+def refine(scene, grads, max_alpha, split_threshold, prune_alpha=1e-3):
+    """Densify and prune (Sec. III-C) a voxel set: a voxel whose largest
+    composited alpha is below prune_alpha is removed; otherwise a voxel below
+    the finest level whose colour-field gradient L1 norm (record slots 4..12)
+    exceeds split_threshold becomes its 8 children (order 0..7, bits x | y << 1
+    | z << 2) carrying its fields; the rest are kept.  Output in input order,
+    children in place of their parent.  Returns (level, ijk, params, actions)
+    with actions 0 keep, 1 split, 2 prune."""
+    level = np.asarray(scene.level).astype(np.int64)
+    ijk = np.asarray(scene.ijk).astype(np.int64)
+    params = np.asarray(scene.params, dtype=np.float64)
+    g1 = np.abs(np.asarray(grads, dtype=np.float64)[:, 4:13]).sum(axis=1)
+    ma = np.asarray(max_alpha, dtype=np.float64)
+    act = np.zeros(len(level), np.int32)
+    act[(level < scene.max_level) & (g1 > split_threshold)] = 1
+    act[ma < prune_alpha] = 2
+    lv, ij, pr = [], [], []
+    for v in range(len(level)):
+        if act[v] == 0:
+            lv.append(level[v]); ij.append(ijk[v]); pr.append(params[v])
+        elif act[v] == 1:
+            for c in range(8):
+                off = np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1])
+                lv.append(level[v] + 1); ij.append(2 * ijk[v] + off)
+                pr.append(subdivide_record(params[v], c))
+    return (np.array(lv, np.uint8), np.array(ij, np.int32).reshape(-1, 3),
+            np.array(pr, np.float64).reshape(-1, 32), act)

@@ -733,6 +733,11 @@ int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
     memset(&rr, 0, sizeof(rr));
     if (valid) {
       composite_ray(s, opt, o, d, tn, tf, &rr);
+      if (out->max_alpha) {
+#pragma omp critical(salf_max_alpha)
+        for (int64_t k = 0; k < rr.n; ++k)
+          if (rr.alpha[k] > out->max_alpha[rr.vox[k]]) out->max_alpha[rr.vox[k]] = rr.alpha[k];
+      }
       for (int64_t k = 0; k < rr.n; ++k) {
         for (int q = 0; q < 3; ++q) C[q] += rr.w[k] * rr.c[3 * k + q];
         D += rr.w[k] * rr.tm[k];
@@ -970,4 +975,30 @@ int orc_render_actors(const orc_scene* s, const orc_actor* actors, int32_t n_act
     free(fd);
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Densification (Sec. III-C)                                                */
+/* ------------------------------------------------------------------------ */
+
+void orc_subdivide_record(const double* rec, int32_t child, double* out) {
+  const double C0 = 0.28209479177387814; /* 1 / (2 sqrt(pi)) */
+  double o[3];
+  for (int a = 0; a < 3; ++a) o[a] = ((child >> a) & 1) ? 1.0 : -1.0;
+  for (int k = 0; k < REC; ++k) out[k] = rec[k];
+  /* geometry W . [x, 1] */
+  out[3] = rec[3] + 0.5 * (rec[0] * o[0] + rec[1] * o[1] + rec[2] * o[2]);
+  for (int a = 0; a < 3; ++a) out[a] = 0.5 * rec[a];
+  /* colour rows: W_c x + W_sh gamma; the constant W_c . o / 2 joins W_sh[r][0] C0 */
+  for (int r = 0; r < 3; ++r) {
+    double shift = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      shift += rec[4 + 3 * r + a] * o[a];
+      out[4 + 3 * r + a] = 0.5 * rec[4 + 3 * r + a];
+    }
+    out[13 + 4 * r] = rec[13 + 4 * r] + 0.5 * shift / C0;
+  }
+  /* intensity W_int . [x, 1] */
+  out[30] = rec[30] + 0.5 * (rec[27] * o[0] + rec[28] * o[1] + rec[29] * o[2]);
+  for (int a = 0; a < 3; ++a) out[27 + a] = 0.5 * rec[27 + a];
 }

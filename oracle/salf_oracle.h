@@ -74,6 +74,7 @@ typedef struct {
   uint8_t* valid;        /* m */
   int32_t* visits;       /* m*visits_cap input voxel indices in order, -1 padded */
   int32_t visits_cap;
+  double* max_alpha;     /* n (input order): largest composited alpha per voxel, max-accumulated */
 } orc_outputs;
 
 typedef struct {
@@ -113,6 +114,14 @@ int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
                  const int64_t* idx, int64_t m, const double* g_rgb, const double* g_depth,
                  const double* g_opacity, const double* g_intensity, double* grad);
 int orc_num_threads(void);
+
+/* Sec. III-C densification: the record of child `child` (bits x | y << 1 |
+ * z << 2 select the upper half per axis) of a voxel split into 8, carrying
+ * the parent's fields: every field is affine in the local coordinates and
+ * x_parent = (x_child + o) / 2 with o in {-1, +1}^3, so slopes halve and the
+ * offsets take W . o / 2 (the colour's, which has no own offset, goes to the
+ * SH DC term through C0).  a and b are kept. */
+void orc_subdivide_record(const double* rec, int32_t child, double* out);
 
 /* Dynamic actors (Sec. IV-A): an actor is a voxel set in its own canonical
  * frame (an orc_scene built from it), placed in the world by pose0 / pose1
