@@ -183,6 +183,9 @@ typedef struct {
   float* ray_dump;
   int32_t* steps;
   int32_t on_host;
+  float* max_alpha;  /* n (scene voxels, input order), device, salf_render_rays only:
+                        max-accumulated with each voxel's largest composited alpha
+                        (Eq. 4) over the rays; the caller zeroes it (pruning, Sec. III-C) */
 } salf_outputs;
 
 typedef struct {
@@ -340,6 +343,40 @@ salf_status salf_render_rays_actors(salf_scene* scene, const salf_actor* actors,
                                     int32_t n_actors, const salf_sensor* sensor,
                                     const salf_render_opts* opts, const salf_outputs* out,
                                     void* stream);
+
+/*
+ * Densification and pruning (Sec. III-C), in two calls.
+ * salf_scene_refine_plan decides per voxel, from `grads` (n x 32 FP32,
+ * dL/d(record scalars), input order, device, 16-byte aligned) and
+ * `max_alpha` (n FP32, input order, device: e.g. salf_outputs.max_alpha of
+ * the training renders):
+ *   - prune if max_alpha < prune_alpha (the paper uses 0.001);
+ *   - else split into 8 octree children if the voxel is above the finest
+ *     level and the L1 norm of its colour-field gradient (record slots 4..12,
+ *     W_c) exceeds split_threshold;
+ *   - else keep.
+ * It waits on `stream` and returns the counts (n_new = n_kept + 8 n_split).
+ * salf_scene_refine_apply then writes the new voxel list, in input order with
+ * children (order 0..7: bits x | y << 1 | z << 2 pick the upper halves) in
+ * place of their parent: level_out (n_new), ijk_out (n_new x 3), params_out
+ * (n_new x 32 FP32, 16-byte aligned), all device memory, from `params` (the
+ * current n x 32 FP32 records, input order, device, 16-byte aligned).  A
+ * child's record carries its parent's fields exactly (all fields are affine
+ * in the local coordinates: slopes halve, offsets take W.o/2, the colour rows'
+ * share goes to their SH DC term).  The result is a voxel set for
+ * salf_build_scene (same grid).  Asynchronous on `stream`.  The plan lives in
+ * a scene-owned workspace until the next plan.  Errors: INVALID (null or
+ * misaligned pointers, apply without a plan), OOM, CUDA.
+ */
+typedef struct {
+  int64_t n_new, n_kept, n_split, n_pruned;
+} salf_refine_counts;
+
+salf_status salf_scene_refine_plan(salf_scene* scene, const float* grads, const float* max_alpha,
+                                   float split_threshold, float prune_alpha,
+                                   salf_refine_counts* counts, void* stream);
+salf_status salf_scene_refine_apply(salf_scene* scene, const float* params, uint8_t* level_out,
+                                    int32_t* ijk_out, float* params_out, void* stream);
 
 /* Check the scene's device status word (synchronises the device).  Returns
  * SALF_ERR_DEVICE if a kernel hit an internal bound since the last check. */

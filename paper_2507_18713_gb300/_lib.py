@@ -48,7 +48,7 @@ class Outputs(C.Structure):
     _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("opacity", c_void_p),
                 ("intensity", c_void_p), ("saved", c_void_p), ("valid", c_void_p),
                 ("visit_count", c_void_p), ("visits", c_void_p), ("ray_dump", c_void_p),
-                ("steps", c_void_p), ("on_host", c_int32)]
+                ("steps", c_void_p), ("on_host", c_int32), ("max_alpha", c_void_p)]
 
 
 class SceneInfo(C.Structure):
@@ -68,6 +68,11 @@ class Actor(C.Structure):
                 ("id_base", c_int32), ("reserved", c_int32)]
 
 
+class RefineCounts(C.Structure):
+    _fields_ = [("n_new", c_int64), ("n_kept", c_int64), ("n_split", c_int64),
+                ("n_pruned", c_int64)]
+
+
 class RasterStats(C.Structure):
     _fields_ = [("visible_voxels", c_int64), ("pairs", c_int64), ("tiles", c_int32),
                 ("key_bits", c_int32), ("kernels", c_int32), ("reserved", c_int32)]
@@ -85,6 +90,10 @@ SIGNATURES = {
                           c_void_p], c_int32),
     "salf_render_rays_actors": ([c_void_p, C.POINTER(Actor), c_int32, C.POINTER(Sensor),
                                  C.POINTER(RenderOpts), C.POINTER(Outputs), c_void_p], c_int32),
+    "salf_scene_refine_plan": ([c_void_p, c_void_p, c_void_p, C.c_float, C.c_float,
+                                C.POINTER(RefineCounts), c_void_p], c_int32),
+    "salf_scene_refine_apply": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p],
+                                c_int32),
     "salf_render_raster": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),
                             C.POINTER(Outputs), C.POINTER(RasterStats), c_void_p], c_int32),
     "salf_render_rays_host_noalloc": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),

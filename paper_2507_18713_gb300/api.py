@@ -82,6 +82,15 @@ def n_rays(sensor: dict) -> int:
     return int(sensor["width"]) * int(sensor["height"])
 
 
+class VoxelSet:
+    """A voxel set on a scene grid (what salf_build_scene takes): origin, s0,
+    dims, max_level, level (n,), ijk (n, 3), params (n, 32), mode."""
+
+    def __init__(self, origin, s0, dims, max_level, level, ijk, params, mode):
+        self.origin, self.s0, self.dims, self.max_level = origin, s0, dims, max_level
+        self.level, self.ijk, self.params, self.mode = level, ijk, params, mode
+
+
 class Scene:
     """A built scene (salf_build_scene).  `scene` is a synth.SceneData (or any
     object with origin, s0, dims, max_level, level, ijk, params, mode)."""
@@ -118,6 +127,9 @@ class Scene:
         self.n = d.n
         self.mode = scene.mode
         self.dtype = dtype
+        self.geometry = dict(origin=tuple(float(v) for v in scene.origin), s0=float(scene.s0),
+                             dims=tuple(int(v) for v in scene.dims),
+                             max_level=int(scene.max_level))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -155,9 +167,11 @@ class Scene:
     def render(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
                visits_cap=0, outputs=("rgb", "depth", "opacity"), saved=False, valid=True,
                stream=None, out: dict | None = None, ray_dump: bool = False,
-               steps: bool = False) -> dict:
+               steps: bool = False, max_alpha=None) -> dict:
         """salf_render_rays into (new or given) CUDA tensors; asynchronous on
-        `stream` (default: torch's current stream)."""
+        `stream` (default: torch's current stream).  `max_alpha` (n float32 CUDA
+        tensor, input order) is max-accumulated with each voxel's largest
+        composited alpha."""
         R = n_rays(sensor)
         dev = torch.device("cuda", self.ctx.device)
         res = {} if out is None else dict(out)
@@ -181,6 +195,9 @@ class Scene:
                   "ray_dump", "steps"):
             if k in res:
                 setattr(o, k, res[k].data_ptr())
+        if max_alpha is not None:
+            assert max_alpha.is_cuda and max_alpha.dtype == torch.float32 and max_alpha.numel() == self.n
+            o.max_alpha = max_alpha.data_ptr()
         keep: list = []
         s = sensor_struct(sensor, keep)
         op = opts_struct(t_min, background, want_intensity, visits_cap)
@@ -227,6 +244,34 @@ class Scene:
             stats.update(visible_voxels=st.visible_voxels, pairs=st.pairs, tiles=st.tiles,
                          key_bits=st.key_bits, kernels=st.kernels)
         return res
+
+    def refine(self, params, grads, max_alpha, split_threshold, prune_alpha=1e-3, stream=None):
+        """Densify and prune (Sec. III-C): salf_scene_refine_plan + apply.  All
+        tensors are CUDA, input order: params and grads (n, 32) float32,
+        max_alpha (n,) float32.  Returns (VoxelSet with the new level / ijk
+        (numpy) and params (CUDA tensor), counts dict)."""
+        lib = L.load()
+        params = params.contiguous().float()
+        grads = grads.contiguous().float()
+        max_alpha = max_alpha.contiguous().float()
+        c = L.RefineCounts()
+        L.check(lib.salf_scene_refine_plan(self._h, grads.data_ptr(), max_alpha.data_ptr(),
+                                           float(split_threshold), float(prune_alpha),
+                                           C.byref(c), _stream_ptr(stream)), "salf_scene_refine_plan")
+        m = int(c.n_new)
+        dev = params.device
+        lv = torch.empty((m,), dtype=torch.uint8, device=dev)
+        ij = torch.empty((m, 3), dtype=torch.int32, device=dev)
+        pr = torch.empty((m, 32), dtype=torch.float32, device=dev)
+        L.check(lib.salf_scene_refine_apply(self._h, params.data_ptr(), lv.data_ptr() if m else None,
+                                            ij.data_ptr() if m else None,
+                                            pr.data_ptr() if m else None, _stream_ptr(stream)),
+                "salf_scene_refine_apply")
+        g = self.geometry
+        vs = VoxelSet(g["origin"], g["s0"], g["dims"], g["max_level"], lv.cpu().numpy(),
+                      ij.cpu().numpy(), pr, self.mode)
+        return vs, dict(n_new=m, n_kept=int(c.n_kept), n_split=int(c.n_split),
+                        n_pruned=int(c.n_pruned))
 
     def render_actors(self, sensor: dict, actors, t_min=1e-4, background=(0.0, 0.0, 0.0),
                       want_intensity=False, visits_cap=0, outputs=("rgb", "depth", "opacity"),

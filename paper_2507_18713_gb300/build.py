@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["render.cu", "backward.cu", "params.cu", "noalloc.cu", "raster.cu", "actors.cu"]
+CUDA_SOURCES = ["render.cu", "backward.cu", "params.cu", "noalloc.cu", "raster.cu", "actors.cu", "refine.cu"]
 CXX_SOURCES = ["capi.cpp", "scene_build.cpp", "serve.cpp"]
 HEADERS = ["salf_internal.h", "traverse.cuh"]
 

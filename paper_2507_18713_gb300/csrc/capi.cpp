@@ -61,6 +61,8 @@ extern "C" void salf_scene_destroy(salf_scene* s) {
   if (s->raster_count_host) cudaFreeHost(s->raster_count_host);
   if (s->raster_done) cudaEventDestroy(s->raster_done);
   if (s->actor_buf) cudaFree(s->actor_buf);
+  if (s->refine_ws) cudaFree(s->refine_ws);
+  if (s->refine_host) cudaFreeHost(s->refine_host);
   if (s->actor_done) cudaEventDestroy(s->actor_done);
   if (s->actor_fork) cudaEventDestroy(s->actor_fork);
   if (s->actor_join) cudaEventDestroy(s->actor_join);
@@ -389,8 +391,8 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
     g_err = "salf_render_rays: visits_cap > 0 needs visits and visit_count";
     return SALF_ERR_INVALID;
   }
-  if (out->on_host && (out->ray_dump || out->steps)) {
-    g_err = "salf_render_rays: ray_dump and steps need device outputs";
+  if (out->on_host && (out->ray_dump || out->steps || out->max_alpha)) {
+    g_err = "salf_render_rays: ray_dump, steps and max_alpha need device outputs";
     return SALF_ERR_INVALID;
   }
   if (!out->on_host && misaligned(out->saved, 16)) {
@@ -422,6 +424,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
     r.visits = out->visits;
     r.ray_dump = out->ray_dump;
     r.steps_out = out->steps;
+    r.max_alpha = reinterpret_cast<unsigned*>(out->max_alpha);
     if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
     return SALF_OK;
   }

@@ -80,9 +80,11 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
     if (hit) {
       const GlobalRec src{reinterpret_cast<const float4*>(S.params) +
                           (size_t)h.vox * RecordLayout<DT>::kChunks};
-      composite_hit<DT, MODE>(w, h, src, want_int, gam, A);
+      const float e = composite_hit<DT, MODE>(w, h, src, want_int, gam, A);
       if (DUMP) {
         if (A.nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + A.nvis] = __ldg(&S.order[h.vox]);
+        if (Q.max_alpha)  // alpha >= 0: FP32 bit patterns order like the values
+          atomicMax(&Q.max_alpha[__ldg(&S.order[h.vox])], __float_as_uint(1.f - e));
       }
       ++A.nvis;
       if (A.T < tmin) w.alive = false;
@@ -120,7 +122,7 @@ cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
   bool dump = false, coherent = true;
   for (int i = 0; i < P.n_req; ++i) {
     const ReqDev& q = P.req[i];
-    dump = dump || q.vcap > 0 || q.ray_dump || q.steps_out;
+    dump = dump || q.vcap > 0 || q.ray_dump || q.steps_out || q.max_alpha;
     coherent = coherent && ((SALF_FWD_COHERENT_KINDS >> q.kind) & 1);
   }
   const int dt = P.S.dtype, md = P.S.mode;

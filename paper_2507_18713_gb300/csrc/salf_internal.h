@@ -105,6 +105,7 @@ struct ReqDev {
   int vcap;
   float* ray_dump;
   int* steps_out;
+  unsigned* max_alpha;  // per voxel (input order): largest alpha, as FP32 bits (alpha >= 0)
   float t_min;
   float bg[3];
   int want_int;
@@ -186,6 +187,13 @@ struct salf_scene {
   void* actor_buf = nullptr;
   size_t actor_buf_bytes = 0;
   cudaEvent_t actor_done = nullptr;
+  // refinement plan workspace (guarded by refine_mu)
+  std::mutex refine_mu;
+  void* refine_ws = nullptr;
+  size_t refine_ws_bytes = 0;
+  unsigned long long* refine_host = nullptr;  // pinned: counts read back
+  bool refine_planned = false;
+  int64_t refine_n_new = 0;
   // the merge kernel runs on this stream beside the ray kernel (fork / join)
   cudaStream_t actor_aux = nullptr;
   cudaEvent_t actor_fork = nullptr, actor_join = nullptr;

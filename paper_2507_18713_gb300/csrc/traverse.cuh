@@ -631,8 +631,9 @@ struct Accum {
 // Composite one hit voxel with its field at the segment midpoint: alpha =
 // 1 - exp(-sigma delta) (Eq. 4), weight T alpha (Eq. 3).  The ray kernel and
 // the tile rasteriser both call this, so their arithmetic is the same.
+// Returns 1 - alpha.
 template <int DT, int MODE, class Src>
-__device__ __forceinline__ void composite_hit(const Walk& w, const Hit& h, const Src& src,
+__device__ __forceinline__ float composite_hit(const Walk& w, const Hit& h, const Src& src,
                                               bool want_int, const float gam[4], Accum& A) {
   const float tm = 0.5f * (h.tin + h.tout);
   const float dl = h.tout - h.tin;
@@ -648,6 +649,7 @@ __device__ __forceinline__ void composite_hit(const Walk& w, const Hit& h, const
   A.Dp = fmaf(wgt, tm, A.Dp);
   A.Ip = fmaf(wgt, f.io, A.Ip);
   A.T *= e;
+  return e;
 }
 
 // Per-ray outputs of a request (colour premultiplied, background added with
