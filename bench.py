@@ -260,6 +260,54 @@ def bench_backward(torch, P, steps, warmup, flush):
                 ms_per_step=avg, mrays_s=len(cams) * R / (avg * 1e-3) / 1e6)
 
 
+def bench_refine(torch, P, flush):
+    """One densify/prune step (Sec. III-C) of the training scene: the 8 training
+    cameras render with alpha maxima and back-propagate an MSE loss, then the
+    top 5% of voxels by colour-gradient L1 norm split, alpha < 0.001 prunes,
+    and the scene is rebuilt from the new voxel list."""
+    sc = synth.driving_scene(1_000_000, seed=4, ground_extent=141.4, n_actors=140)
+    g = P.Scene(sc, dtype="bf16")
+    cams = [synth.pinhole(960, 640, 60.0, synth.camera_pose_looking(
+        (5.0 * math.cos(k * math.pi / 4), 5.0 * math.sin(k * math.pi / 4), 1.7), k * math.pi / 4))
+        for k in range(8)]
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    R = 960 * 640
+    params = torch.from_numpy(sc.params.astype(np.float32)).cuda()
+    dparams = torch.zeros((sc.n, 32), device="cuda")
+    ma = torch.zeros(sc.n, device="cuda")
+    for cam in cams:
+        o = g.render(cam, outputs=("rgb",), saved=True, valid=False, max_alpha=ma)
+        tg = torch.rand((R, 3), device="cuda", generator=gen)
+        g.backward(cam, o["saved"], d_rgb=(o["rgb"] - tg).mul_(2.0 / (R * 3 * len(cams))),
+                   d_params=dparams)
+    l1 = dparams[:, 4:13].abs().sum(dim=1)
+    thr = float(torch.quantile(l1[l1 > 0][:1 << 24].float(), 0.95).item())
+    torch.cuda.synchronize()
+    ms = {}
+    reps = 5
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vs, counts = g.refine(params, dparams, ma, thr, 1e-3)
+        t1 = time.perf_counter()
+        g2 = P.Scene(vs, dtype="bf16", params=vs.params)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        ms.setdefault("plan_apply", []).append((t1 - t0) * 1e3)
+        ms.setdefault("rebuild", []).append((t2 - t1) * 1e3)
+        g2.close()
+    g.check()
+    return dict(workload="training scene 1,000,000 voxels (seed 4), BF16; alpha maxima and "
+                "gradients from the 8 training cameras (960x640); split the top 5% by colour-"
+                "gradient L1 norm, prune alpha < 0.001",
+                counts=counts, split_threshold=thr,
+                plan_apply_ms=statistics.median(ms["plan_apply"]),
+                rebuild_ms=statistics.median(ms["rebuild"]),
+                note="plan + apply on the GPU (includes the one host wait for the counts); rebuild "
+                     "= level/ijk to the host and salf_build_scene (host build, records on the GPU)")
+
+
 def bench_serving(torch, P, duration_s=5.0, seed=6):
     sc = synth.driving_scene(4_000_000, seed=3, ground_layers=2, n_actors=600)
     g = P.Scene(sc, dtype="bf16")
@@ -639,6 +687,8 @@ def main():
         del g
         torch.cuda.empty_cache()
         extra("train_step", lambda: bench_backward(torch, P, args.steps, args.warmup, flush))
+        torch.cuda.empty_cache()
+        extra("refine", lambda: bench_refine(torch, P, flush))
         torch.cuda.empty_cache()
         extra("serving", lambda: bench_serving(torch, P, args.serve_seconds))
 
