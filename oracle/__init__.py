@@ -14,6 +14,8 @@ from .oracle import (  # noqa: F401
     render_actors,
     refine,
     subdivide_record,
+    face_pairs,
+    reg_loss,
     backward,
     gen_rays,
     trace,

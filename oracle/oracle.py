@@ -382,3 +382,106 @@ def refine(scene, grads, max_alpha, split_threshold, prune_alpha=1e-3):
                 pr.append(subdivide_record(params[v], c))
     return (np.array(lv, np.uint8), np.array(ij, np.int32).reshape(-1, 3),
             np.array(pr, np.float64).reshape(-1, 32), act)
+
+
+def _density_and_grad(g, rec, mode):
+    """sigma(g) and d sigma / d(g, a, b) for the geometry value g (Eq. 1 / Eq. 6)."""
+    if mode == "exp":
+        s = np.exp(g)
+        return s, s, 0.0, 0.0
+    a, b = rec[25], rec[26]
+    e = np.exp(-abs(g) / b)
+    sg = np.sign(g)
+    s = 0.5 * a + 0.5 * a * sg * (1.0 - e)
+    ds_dg = 0.5 * a * e / b
+    ds_da = s / a
+    ds_db = -0.5 * a * g * e / (b * b)
+    return s, ds_dg, ds_da, ds_db
+
+
+def face_pairs(scene):
+    """Face-adjacent voxel pairs (positive contact area), brute force:
+    list of (i, j, axis, sign) with voxel j on the `sign` side of voxel i
+    along `axis`, i no larger than j (one entry per pair)."""
+    K = scene.max_level
+    lvl = np.asarray(scene.level).astype(np.int64)
+    e = (1 << (K - lvl)).astype(np.int64)                       # edges in finest cells
+    lo = np.asarray(scene.ijk).astype(np.int64) * e[:, None]
+    hi = lo + e[:, None]
+    out = []
+    n = len(lvl)
+    for i in range(n):
+        for j in range(n):
+            if i == j or e[j] < e[i] or (e[j] == e[i] and j < i):
+                continue
+            for a in range(3):
+                o = [b for b in range(3) if b != a]
+                area = all(min(hi[i, b], hi[j, b]) > max(lo[i, b], lo[j, b]) for b in o)
+                if not area:
+                    continue
+                if hi[i, a] == lo[j, a]:
+                    out.append((i, j, a, +1))
+                elif lo[i, a] == hi[j, a]:
+                    out.append((i, j, a, -1))
+    return out
+
+
+def reg_loss(scene, params, lam_s, lam_alpha, lam_n):
+    """Eq. 7's L_reg and its gradient w.r.t. the records (n x 32), over the
+    face-adjacent pairs (i, j): lam_s |s_i - s_j| + lam_alpha |alpha_i -
+    alpha_j| + lam_n (1 - n_i . n_j), where, at the centre X of the shared face
+    (the smaller voxel's face): s_k = W_k . [x_k(X), 1] (record slots 0..3),
+    alpha_k = 1 - exp(-sigma_k(s_k) l) with l the smaller voxel's edge (m), and
+    n_k = W_k[0:3] / |W_k[0:3]| (0 if that is 0)."""
+    K = scene.max_level
+    sfin = scene.s0 / (1 << K)
+    lvl = np.asarray(scene.level).astype(np.int64)
+    e = (1 << (K - lvl)).astype(np.int64)
+    lo = np.asarray(scene.ijk).astype(np.int64) * e[:, None]
+    P = np.asarray(params, dtype=np.float64)
+    grad = np.zeros_like(P)
+    loss = 0.0
+    for i, j, a, sgn in face_pairs(scene):
+        X = lo[i] + 0.5 * e[i]
+        X = X.astype(np.float64)
+        X[a] += 0.5 * e[i] * sgn                               # centre of i's face towards j
+        xs, ss, sig, dsg = [], [], [], []
+        for k in (i, j):
+            x = (X - (lo[k] + 0.5 * e[k])) / (0.5 * e[k])
+            s = P[k, :3] @ x + P[k, 3]
+            xs.append(x)
+            ss.append(s)
+            sk, ds_dg, ds_da, ds_db = _density_and_grad(s, P[k], scene.mode)
+            sig.append(sk)
+            dsg.append((ds_dg, ds_da, ds_db))
+        ell = e[i] * sfin
+        # s term
+        d = ss[0] - ss[1]
+        loss += lam_s * abs(d)
+        for k, x, sg in ((i, xs[0], 1.0), (j, xs[1], -1.0)):
+            grad[k, :3] += lam_s * np.sign(d) * sg * x
+            grad[k, 3] += lam_s * np.sign(d) * sg
+        # alpha term
+        al = [1.0 - np.exp(-sig[q] * ell) for q in (0, 1)]
+        da = al[0] - al[1]
+        loss += lam_alpha * abs(da)
+        for q, k, sg in ((0, i, 1.0), (1, j, -1.0)):
+            dal_dsig = np.exp(-sig[q] * ell) * ell
+            c = lam_alpha * np.sign(da) * sg * dal_dsig
+            ds_dg, ds_da, ds_db = dsg[q]
+            grad[k, :3] += c * ds_dg * xs[q]
+            grad[k, 3] += c * ds_dg
+            if scene.mode == "sdf":
+                grad[k, 25] += c * ds_da
+                grad[k, 26] += c * ds_db
+        # normal term
+        w = [P[i, :3], P[j, :3]]
+        nn = [np.linalg.norm(v) for v in w]
+        nv = [w[q] / nn[q] if nn[q] > 0 else np.zeros(3) for q in (0, 1)]
+        loss += lam_n * (1.0 - nv[0] @ nv[1])
+        for q, k in ((0, i), (1, j)):
+            if nn[q] > 0:
+                other = nv[1 - q]
+                # d(n . m)/dw = (m - n (n . m)) / |w|
+                grad[k, :3] += -lam_n * (other - nv[q] * (nv[q] @ other)) / nn[q]
+    return loss, grad

@@ -103,3 +103,60 @@ def test_max_alpha_is_the_largest_composited_alpha(oracle_lib):
             ref[v] = max(ref[v], 1.0 - math.exp(-sig * (b - max(a, 0.0))))
     assert (ma > 0).sum() > 10
     assert np.abs(ma - ref).max() < 1e-12
+
+
+def _affine_params(sc, A, c, rng):
+    """Records whose geometry field is the restriction of one global affine
+    field G(X) = A . X + c (X in metres)."""
+    P = rng.normal(size=(len(sc.level), 32)) * 0.1
+    if sc.mode == "sdf":
+        P[:, 25] = 1.5
+        P[:, 26] = 0.3
+    for k in range(len(sc.level)):
+        e = sc.s0 / (1 << int(sc.level[k]))
+        ctr = np.asarray(sc.origin) + (sc.ijk[k] + 0.5) * e
+        P[k, :3] = A * (0.5 * e)
+        P[k, 3] = A @ ctr + c
+    return P
+
+
+def test_reg_pairs_known_configurations(oracle_lib):
+    cells = [(i, j, k) for i in range(2) for j in range(2) for k in range(2)]
+    block = synth.single_voxel_scene(np.zeros((8, 32)), dims=(2, 2, 2), cells=cells, levels=[0] * 8)
+    assert len(oracle_lib.face_pairs(block)) == 12
+    # a level-0 voxel facing four level-1 voxels across its +x face
+    cells = [(0, 0, 0)] + [(2, j, k) for j in range(2) for k in range(2)]
+    mixed = synth.single_voxel_scene(np.zeros((5, 32)), dims=(2, 1, 1), cells=cells,
+                                     levels=[0, 1, 1, 1, 1], max_level=1)
+    pairs = oracle_lib.face_pairs(mixed)
+    assert len(pairs) == 8  # 4 big-small, 4 among the small ones
+    assert sum(1 for p in pairs if p[0] == 0 or p[1] == 0) == 4
+
+
+def test_reg_vanishes_for_a_global_affine_field(oracle_lib):
+    rng = np.random.default_rng(3)
+    for mode in ("exp", "sdf"):
+        sc = synth.random_multilevel_scene(seed=4, max_level=2, dims=(4, 3, 3), p_occ=0.7, mode=mode)
+        P = _affine_params(sc, np.array([0.3, -0.2, 0.5]), 0.1, rng)
+        loss, _ = oracle_lib.reg_loss(sc, P, 1.0, 1.0, 1.0)
+        assert len(oracle_lib.face_pairs(sc)) > 40
+        assert abs(loss) < 1e-9, loss
+
+
+def test_reg_gradient_matches_finite_differences(oracle_lib):
+    rng = np.random.default_rng(5)
+    for mode in ("exp", "sdf"):
+        sc = synth.random_multilevel_scene(seed=5, max_level=2, dims=(3, 3, 2), p_occ=0.7, mode=mode)
+        P = np.asarray(sc.params, dtype=np.float64).copy()
+        lam = (0.7, 1.3, 0.4)
+        _, grad = oracle_lib.reg_loss(sc, P, *lam)
+        cols = [0, 1, 2, 3] + ([25, 26] if mode == "sdf" else [])
+        for v in rng.choice(len(P), size=8, replace=False):
+            for c in cols:
+                h = 1e-6
+                Pp, Pm = P.copy(), P.copy()
+                Pp[v, c] += h
+                Pm[v, c] -= h
+                fd = (oracle_lib.reg_loss(sc, Pp, *lam)[0] - oracle_lib.reg_loss(sc, Pm, *lam)[0]) / (2 * h)
+                assert abs(fd - grad[v, c]) <= 1e-5 * max(1.0, abs(fd)), (mode, v, c, fd, grad[v, c])
+        assert np.all(grad[:, 4:25] == 0) and np.all(grad[:, 27:] == 0)
