@@ -378,6 +378,23 @@ salf_status salf_scene_refine_plan(salf_scene* scene, const float* grads, const 
 salf_status salf_scene_refine_apply(salf_scene* scene, const float* params, uint8_t* level_out,
                                     int32_t* ijk_out, float* params_out, void* stream);
 
+/*
+ * L_reg of Eq. 7 over the face-adjacent voxel pairs of the scene, from the
+ * records `params` (n x 32 FP32, input order, device, 16-byte aligned):
+ *   sum over pairs (i, j) of lambda_s |s_i - s_j| + lambda_alpha |alpha_i -
+ *   alpha_j| + lambda_n (1 - n_i . n_j),
+ * where, at the centre of the shared face (the smaller voxel's face), s_k is
+ * the geometry field W_k . [x_k, 1] (record slots 0..3: W_sigma or W_s),
+ * alpha_k = 1 - exp(-sigma_k l) with sigma_k its density (Eq. 1 or Eq. 6) and
+ * l the smaller voxel's edge in metres, and n_k = W_k[0:3] / |W_k[0:3]| (0 if
+ * that is 0).  *loss (one float, device) and grads (n x 32 FP32, input order,
+ * device) are ACCUMULATED (+=); |.| takes sign(0) = 0 as its slope.
+ * Asynchronous on `stream`.  Errors: INVALID, CUDA.
+ */
+salf_status salf_scene_reg_loss(salf_scene* scene, const float* params, float lambda_s,
+                                float lambda_alpha, float lambda_n, float* loss, float* grads,
+                                void* stream);
+
 /* Check the scene's device status word (synchronises the device).  Returns
  * SALF_ERR_DEVICE if a kernel hit an internal bound since the last check. */
 salf_status salf_scene_check(salf_scene* scene);

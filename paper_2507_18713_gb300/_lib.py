@@ -94,6 +94,8 @@ SIGNATURES = {
                                 C.POINTER(RefineCounts), c_void_p], c_int32),
     "salf_scene_refine_apply": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p],
                                 c_int32),
+    "salf_scene_reg_loss": ([c_void_p, c_void_p, C.c_float, C.c_float, C.c_float, c_void_p,
+                             c_void_p, c_void_p], c_int32),
     "salf_render_raster": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),
                             C.POINTER(Outputs), C.POINTER(RasterStats), c_void_p], c_int32),
     "salf_render_rays_host_noalloc": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),

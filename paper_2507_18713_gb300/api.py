@@ -273,6 +273,21 @@ class Scene:
         return vs, dict(n_new=m, n_kept=int(c.n_kept), n_split=int(c.n_split),
                         n_pruned=int(c.n_pruned))
 
+    def reg_loss(self, params, lambda_s, lambda_alpha, lambda_n, grads=None, loss=None,
+                 stream=None):
+        """salf_scene_reg_loss (Eq. 7 L_reg): returns (loss (1,) CUDA tensor,
+        grads (n, 32)), both accumulated into the given tensors if any."""
+        params = params.contiguous().float()
+        if grads is None:
+            grads = torch.zeros((self.n, 32), dtype=torch.float32, device=params.device)
+        if loss is None:
+            loss = torch.zeros((1,), dtype=torch.float32, device=params.device)
+        L.check(L.load().salf_scene_reg_loss(self._h, params.data_ptr(), float(lambda_s),
+                                             float(lambda_alpha), float(lambda_n), loss.data_ptr(),
+                                             grads.data_ptr(), _stream_ptr(stream)),
+                "salf_scene_reg_loss")
+        return loss, grads
+
     def render_actors(self, sensor: dict, actors, t_min=1e-4, background=(0.0, 0.0, 0.0),
                       want_intensity=False, visits_cap=0, outputs=("rgb", "depth", "opacity"),
                       saved=False, valid=True, stream=None, out: dict | None = None) -> dict:

@@ -15,8 +15,8 @@
 #include <cstring>
 #include <mutex>
 
-#include "salf_internal.h"
 #include "scan.cuh"
+#include "traverse.cuh"
 
 using namespace salf_scan;
 
@@ -112,6 +112,127 @@ __global__ void __launch_bounds__(256) k_refine_apply(
     for (int k = 0; k < 8; ++k)
       dst[k] = make_float4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
   }
+}
+
+// Density of the geometry value g (Eq. 1 or Eq. 6) and its derivatives with
+// respect to g, a and b.
+template <int MODE>
+__device__ __forceinline__ float reg_density(float g, float a, float b, float* d_g, float* d_a,
+                                             float* d_b) {
+  if (MODE == SALF_FIELD_EXP) {
+    const float s = __expf(g);
+    *d_g = s;
+    *d_a = *d_b = 0.f;
+    return s;
+  }
+  const float e = __expf(-fabsf(g) / b);
+  const float sg = g > 0.f ? 1.f : (g < 0.f ? -1.f : 0.f);
+  const float s = 0.5f * a + 0.5f * a * sg * (1.f - e);
+  *d_g = 0.5f * a * e / b;
+  *d_a = s / a;
+  *d_b = -0.5f * a * g * e / (b * b);
+  return s;
+}
+
+// Eq. 7's L_reg over the face-adjacent pairs, one thread per voxel: across
+// each face, the voxel owning the finest cell just outside its min corner is
+// the neighbour when it is at least as large (then it covers the whole face);
+// a pair is counted by its smaller voxel, or by the + face of the one on the
+// - side when both are equal.  At the centre of the shared face: s = W.[x,1],
+// alpha = 1 - exp(-sigma(s) l) (l: the smaller edge, m), n = W[0:3] / |W[0:3]|.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_reg_loss(const __grid_constant__ DevScene S,
+                                                  const float* __restrict__ params, float lam_s,
+                                                  float lam_a, float lam_n, float sfin,
+                                                  float* __restrict__ loss,
+                                                  float* __restrict__ grads) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  float acc = 0.f;
+  if (p < S.n) {
+    const int4 bi = __ldg(&S.vox_box[p]);
+    const int E = 1 << bi.w;
+    const int lo[3] = {bi.x, bi.y, bi.z};
+    const int vi = __ldg(&S.order[p]);
+    const float4 wi = __ldg(reinterpret_cast<const float4*>(params) + (size_t)vi * 8);
+    const float4 abi = __ldg(reinterpret_cast<const float4*>(params) + (size_t)vi * 8 + 6);
+    const float Wi[4] = {wi.x, wi.y, wi.z, wi.w};
+    const float ni = sqrtf(Wi[0] * Wi[0] + Wi[1] * Wi[1] + Wi[2] * Wi[2]);
+    for (int f = 0; f < 6; ++f) {
+      const int ax = f >> 1;
+      const int sgn = (f & 1) ? 1 : -1;
+      int c[3] = {lo[0], lo[1], lo[2]};
+      c[ax] = sgn > 0 ? lo[ax] + E : lo[ax] - 1;
+      if (c[ax] < 0 || c[ax] >= S.Gf[ax]) continue;
+      int lsj;
+      const int j = salf::find_leaf(S, c[0], c[1], c[2], &lsj);
+      if (j < 0 || lsj < bi.w || (lsj == bi.w && sgn < 0)) continue;
+      const int4 bj = __ldg(&S.vox_box[j]);
+      const int Ej = 1 << bj.w;
+      const int vj = __ldg(&S.order[j]);
+      const float4 wj = __ldg(reinterpret_cast<const float4*>(params) + (size_t)vj * 8);
+      const float4 abj = __ldg(reinterpret_cast<const float4*>(params) + (size_t)vj * 8 + 6);
+      const float Wj[4] = {wj.x, wj.y, wj.z, wj.w};
+      // local coordinates of the face centre: +-1 on the axis in i; in j from its box
+      float xi[3] = {0.f, 0.f, 0.f}, xj[3];
+      xi[ax] = (float)sgn;
+      const int lj[3] = {bj.x, bj.y, bj.z};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float X = a == ax ? (float)(sgn > 0 ? lo[a] + E : lo[a]) : (float)lo[a] + 0.5f * E;
+        xj[a] = (X - ((float)lj[a] + 0.5f * Ej)) / (0.5f * Ej);
+      }
+      const float si = Wi[0] * xi[0] + Wi[1] * xi[1] + Wi[2] * xi[2] + Wi[3];
+      const float sj = Wj[0] * xj[0] + Wj[1] * xj[1] + Wj[2] * xj[2] + Wj[3];
+      float gi_g, gi_a, gi_b, gj_g, gj_a, gj_b;
+      const float sigi = reg_density<MODE>(si, abi.y, abi.z, &gi_g, &gi_a, &gi_b);
+      const float sigj = reg_density<MODE>(sj, abj.y, abj.z, &gj_g, &gj_a, &gj_b);
+      const float ell = (float)E * sfin;
+      const float ei = __expf(-sigi * ell), ej = __expf(-sigj * ell);
+      const float ds = si - sj, da = ej - ei;  // alpha_i - alpha_j = e_j - e_i
+      const float nj = sqrtf(Wj[0] * Wj[0] + Wj[1] * Wj[1] + Wj[2] * Wj[2]);
+      float ui[3] = {0.f, 0.f, 0.f}, uj[3] = {0.f, 0.f, 0.f};
+      if (ni > 0.f)
+        for (int a = 0; a < 3; ++a) ui[a] = Wi[a] / ni;
+      if (nj > 0.f)
+        for (int a = 0; a < 3; ++a) uj[a] = Wj[a] / nj;
+      const float dot = ui[0] * uj[0] + ui[1] * uj[1] + ui[2] * uj[2];
+      acc += lam_s * fabsf(ds) + lam_a * fabsf(da) + lam_n * (1.f - dot);
+      const float cs = lam_s * (ds > 0.f ? 1.f : (ds < 0.f ? -1.f : 0.f));
+      const float ca = lam_a * (da > 0.f ? 1.f : (da < 0.f ? -1.f : 0.f));
+      // d alpha_k / d sigma_k = exp(-sigma_k l) l
+      const float ki = ca * ei * ell, kj = -ca * ej * ell;
+      float gi[6], gj[6];  // slots 0..3, a, b
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        gi[a] = cs * xi[a] + ki * gi_g * xi[a];
+        gj[a] = -cs * xj[a] + kj * gj_g * xj[a];
+        if (ni > 0.f) gi[a] -= lam_n * (uj[a] - ui[a] * dot) / ni;
+        if (nj > 0.f) gj[a] -= lam_n * (ui[a] - uj[a] * dot) / nj;
+      }
+      gi[3] = cs + ki * gi_g;
+      gj[3] = -cs + kj * gj_g;
+      gi[4] = ki * gi_a;
+      gi[5] = ki * gi_b;
+      gj[4] = kj * gj_a;
+      gj[5] = kj * gj_b;
+      float* Gi = grads + (size_t)vi * 32;
+      float* Gj = grads + (size_t)vj * 32;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        atomicAdd(Gi + q, gi[q]);
+        atomicAdd(Gj + q, gj[q]);
+      }
+      if (MODE == SALF_FIELD_SDF) {
+        atomicAdd(Gi + 25, gi[4]);
+        atomicAdd(Gi + 26, gi[5]);
+        atomicAdd(Gj + 25, gj[4]);
+        atomicAdd(Gj + 26, gj[5]);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.f) atomicAdd(loss, acc);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -226,6 +347,35 @@ extern "C" salf_status salf_scene_refine_apply(salf_scene* sc, const float* para
     k_refine_apply<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         D.vox_box, D.order, (int)n, D.K, action, offs, params, level_out, ijk_out, params_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return salf_cuda_fail(e, "refine apply");
+  }
+  return SALF_OK;
+}
+
+extern "C" salf_status salf_scene_reg_loss(salf_scene* sc, const float* params, float lambda_s,
+                                          float lambda_alpha, float lambda_n, float* loss,
+                                          float* grads, void* stream) {
+  if (!sc || !params || !loss || !grads) {
+    salf_set_error("salf_scene_reg_loss: null argument");
+    return SALF_ERR_INVALID;
+  }
+  if (misaligned16(params)) {
+    salf_set_error("salf_scene_reg_loss: params must be 16-byte aligned");
+    return SALF_ERR_INVALID;
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  const DevScene& D = sc->dev;
+  if (D.n > 0) {
+    const unsigned blocks = (unsigned)((D.n + 255) / 256);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float sfin = (float)sc->sfin;
+    if (D.mode == SALF_FIELD_EXP)
+      k_reg_loss<SALF_FIELD_EXP><<<blocks, 256, 0, st>>>(D, params, lambda_s, lambda_alpha,
+                                                          lambda_n, sfin, loss, grads);
+    else
+      k_reg_loss<SALF_FIELD_SDF><<<blocks, 256, 0, st>>>(D, params, lambda_s, lambda_alpha,
+                                                          lambda_n, sfin, loss, grads);
+    if ((e = cudaGetLastError()) != cudaSuccess) return salf_cuda_fail(e, "reg loss launch");
   }
   return SALF_OK;
 }

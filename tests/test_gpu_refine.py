@@ -101,3 +101,36 @@ def test_refine_edge_cases(salf):
     g2 = salf.Scene(sc)
     st = salf.load().salf_scene_refine_apply(g2._h, params.data_ptr(), None, None, None, None)
     assert st == 1  # SALF_ERR_INVALID
+
+
+@pytest.mark.parametrize("mode", ["exp", "sdf"])
+def test_reg_loss_matches_oracle(salf, oracle_lib, mode):
+    """L_reg of Eq. 7 and its gradient, GPU vs the oracle's pair sums."""
+    sc = synth.random_multilevel_scene(seed=8, max_level=2, dims=(6, 5, 4), p_occ=0.6, mode=mode)
+    g = salf.Scene(sc)
+    P = np.asarray(sc.params, dtype=np.float32)
+    lam = (0.7, 1.3, 0.4)
+    loss, grads = g.reg_loss(torch.from_numpy(P).cuda(), *lam)
+    torch.cuda.synchronize()
+    ref_loss, ref_grad = oracle_lib.reg_loss(sc, P.astype(np.float64), *lam)
+    assert len(oracle_lib.face_pairs(sc)) > 200
+    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * abs(ref_loss)
+    gg = to_np(grads).astype(np.float64)
+    assert np.abs(gg - ref_grad).max() <= 1e-4 * max(1.0, np.abs(ref_grad).max())
+
+
+def test_reg_loss_vanishes_for_global_affine_field(salf):
+    sc = synth.random_multilevel_scene(seed=4, max_level=2, dims=(6, 5, 4), p_occ=0.7, mode="sdf")
+    rng = np.random.default_rng(3)
+    A, c = np.array([0.3, -0.2, 0.5]), 0.1
+    P = rng.normal(size=(len(sc.level), 32)).astype(np.float64) * 0.1
+    P[:, 25], P[:, 26] = 1.5, 0.3
+    for k in range(len(sc.level)):
+        e = sc.s0 / (1 << int(sc.level[k]))
+        ctr = np.asarray(sc.origin) + (sc.ijk[k] + 0.5) * e
+        P[k, :3] = A * (0.5 * e)
+        P[k, 3] = A @ ctr + c
+    g = salf.Scene(sc)
+    loss, _ = g.reg_loss(torch.from_numpy(P.astype(np.float32)).cuda(), 1.0, 1.0, 1.0)
+    torch.cuda.synchronize()
+    assert abs(float(loss.item())) < 1e-3
