@@ -297,11 +297,15 @@ def bench_refine(torch, P, flush):
         ms.setdefault("plan_apply", []).append((t1 - t0) * 1e3)
         ms.setdefault("rebuild", []).append((t2 - t1) * 1e3)
         g2.close()
+    # Eq. 7 L_reg over the scene's face-adjacent pairs (loss and gradient)
+    loss = torch.zeros(1, device="cuda")
+    reg = statistics.median(timed_renders(
+        torch, lambda: g.reg_loss(params, 1.0, 1.0, 1.0, grads=dparams, loss=loss), 20, 3, flush))
     g.check()
     return dict(workload="training scene 1,000,000 voxels (seed 4), BF16; alpha maxima and "
                 "gradients from the 8 training cameras (960x640); split the top 5% by colour-"
                 "gradient L1 norm, prune alpha < 0.001",
-                counts=counts, split_threshold=thr,
+                counts=counts, split_threshold=thr, reg_loss_ms=reg,
                 plan_apply_ms=statistics.median(ms["plan_apply"]),
                 rebuild_ms=statistics.median(ms["rebuild"]),
                 note="plan + apply on the GPU (includes the one host wait for the counts); rebuild "
