@@ -309,7 +309,7 @@ def bench_refine(torch, P, flush):
                 plan_apply_ms=statistics.median(ms["plan_apply"]),
                 rebuild_ms=statistics.median(ms["rebuild"]),
                 note="plan + apply on the GPU (includes the one host wait for the counts); rebuild "
-                     "= level/ijk to the host and salf_build_scene (host build, records on the GPU)")
+                     "= salf_build_scene from the device-resident voxel list (device build)")
 
 
 def bench_serving(torch, P, duration_s=5.0, seed=6):

@@ -85,8 +85,10 @@ typedef struct salf_server salf_server;
  * `params` are FP32 (host memory, or device memory if params_on_device);
  * `dtype` selects how the scene stores them (FP32, or BF16 converted by
  * round-to-nearest; all arithmetic is FP32 either way).  level and ijk are
- * host memory.  Everything is copied: the caller may free its arrays when
- * salf_build_scene returns.
+ * host memory, unless keys_on_device: then level, ijk and params are device
+ * memory (params_on_device must be set) and the whole build runs on the GPU
+ * (same structure, same errors).  Everything is copied: the caller may free
+ * its arrays when salf_build_scene returns.
  */
 typedef struct {
   int64_t n;
@@ -100,6 +102,7 @@ typedef struct {
   int32_t dtype;  /* salf_dtype */
   const float* params;
   int32_t params_on_device;
+  int32_t keys_on_device;
 } salf_scene_desc;
 
 /*
@@ -196,7 +199,7 @@ typedef struct {
   int64_t n_level0_cells;   /* occupied level-0 cells */
   int64_t n_nodes;          /* subdivision nodes below level 0 */
   int64_t device_bytes;     /* device memory held by the scene */
-  const void* dev_params;   /* records in the scene's internal (Morton) order */
+  const void* dev_params;   /* records in the scene's internal voxel order */
   const int32_t* dev_order; /* internal index -> input index */
 } salf_scene_info;
 

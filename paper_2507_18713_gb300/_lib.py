@@ -27,7 +27,8 @@ DTYPE = {"f32": 0, "bf16": 1}
 class SceneDesc(C.Structure):
     _fields_ = [("n", c_int64), ("origin", c_double * 3), ("s0", c_double), ("dims", c_int32 * 3),
                 ("max_level", c_int32), ("level", c_void_p), ("ijk", c_void_p), ("mode", c_int32),
-                ("dtype", c_int32), ("params", c_void_p), ("params_on_device", c_int32)]
+                ("dtype", c_int32), ("params", c_void_p), ("params_on_device", c_int32),
+                ("keys_on_device", c_int32)]
 
 
 class Sensor(C.Structure):

@@ -98,9 +98,16 @@ class Scene:
     def __init__(self, scene, dtype: str = "f32", ctx: Context | None = None, params=None):
         self.ctx = ctx or Context.default()
         lib = L.load()
-        level = np.ascontiguousarray(scene.level, dtype=np.uint8)
-        ijk = np.ascontiguousarray(scene.ijk, dtype=np.int32)
         p = scene.params if params is None else params
+        keys_dev = isinstance(scene.level, torch.Tensor) and scene.level.is_cuda
+        if keys_dev:  # the whole build runs on the GPU
+            level = scene.level.contiguous().to(torch.uint8)
+            ijk = scene.ijk.contiguous().to(torch.int32)
+            if not (isinstance(p, torch.Tensor) and p.is_cuda):
+                p = torch.as_tensor(np.asarray(p, dtype=np.float32), device=level.device)
+        else:
+            level = np.ascontiguousarray(scene.level, dtype=np.uint8)
+            ijk = np.ascontiguousarray(scene.ijk, dtype=np.int32)
         on_dev = isinstance(p, torch.Tensor) and p.is_cuda
         if on_dev:
             p = p.contiguous().float()
@@ -110,17 +117,21 @@ class Scene:
             p = np.ascontiguousarray(p, dtype=np.float32)
         d = L.SceneDesc()
         d.n = int(level.shape[0])
+        d.keys_on_device = int(keys_dev)
         d.origin[:] = [float(v) for v in scene.origin]
         d.s0 = float(scene.s0)
         d.dims[:] = [int(v) for v in scene.dims]
         d.max_level = int(scene.max_level)
-        d.level, d.ijk = level.ctypes.data, ijk.ctypes.data
+        if keys_dev:
+            d.level, d.ijk = level.data_ptr(), ijk.data_ptr()
+        else:
+            d.level, d.ijk = level.ctypes.data, ijk.ctypes.data
         d.mode = L.MODE[scene.mode]
         d.dtype = L.DTYPE[dtype]
         d.params = p.data_ptr() if on_dev else p.ctypes.data
         d.params_on_device = int(on_dev)
         h = C.c_void_p()
-        if on_dev:
+        if on_dev or keys_dev:
             torch.cuda.synchronize()
         L.check(lib.salf_build_scene(self.ctx._h, C.byref(d), C.byref(h)), "salf_build_scene")
         self._h = h
@@ -249,7 +260,7 @@ class Scene:
         """Densify and prune (Sec. III-C): salf_scene_refine_plan + apply.  All
         tensors are CUDA, input order: params and grads (n, 32) float32,
         max_alpha (n,) float32.  Returns (VoxelSet with the new level / ijk
-        (numpy) and params (CUDA tensor), counts dict)."""
+        / params as CUDA tensors, which Scene() builds on the GPU, counts dict)."""
         lib = L.load()
         params = params.contiguous().float()
         grads = grads.contiguous().float()
@@ -268,8 +279,7 @@ class Scene:
                                             pr.data_ptr() if m else None, _stream_ptr(stream)),
                 "salf_scene_refine_apply")
         g = self.geometry
-        vs = VoxelSet(g["origin"], g["s0"], g["dims"], g["max_level"], lv.cpu().numpy(),
-                      ij.cpu().numpy(), pr, self.mode)
+        vs = VoxelSet(g["origin"], g["s0"], g["dims"], g["max_level"], lv, ij, pr, self.mode)
         return vs, dict(n_new=m, n_kept=int(c.n_kept), n_split=int(c.n_split),
                         n_pruned=int(c.n_pruned))
 

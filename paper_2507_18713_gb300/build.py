@@ -19,9 +19,10 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["render.cu", "backward.cu", "params.cu", "noalloc.cu", "raster.cu", "actors.cu", "refine.cu"]
+CUDA_SOURCES = ["render.cu", "backward.cu", "params.cu", "noalloc.cu", "raster.cu", "actors.cu",
+                "refine.cu", "scene_build_gpu.cu"]
 CXX_SOURCES = ["capi.cpp", "scene_build.cpp", "serve.cpp"]
-HEADERS = ["salf_internal.h", "traverse.cuh"]
+HEADERS = ["salf_internal.h", "traverse.cuh", "scan.cuh", "sort.cuh"]
 
 
 def _nvcc() -> str:

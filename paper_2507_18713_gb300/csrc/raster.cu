@@ -28,10 +28,12 @@
 #include <mutex>
 
 #include "scan.cuh"
+#include "sort.cuh"
 #include "traverse.cuh"
 
 using namespace salf;
 using namespace salf_scan;
+using namespace salf_sort;
 
 namespace {
 
@@ -45,11 +47,6 @@ constexpr int kRasterThreads = kTile * kTile;
 #define SALF_RASTER_CHUNK 128
 #endif
 constexpr int kChunk = SALF_RASTER_CHUNK;  // voxels staged in shared memory at a time
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;      // rounds per block
-constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
 
 struct ProjParams {
   DevScene S;
@@ -192,82 +189,6 @@ __global__ void __launch_bounds__(256) k_emit(const unsigned* __restrict__ count
       out_key[o] = ((unsigned long long)(ty * tiles_x + tx) << key_bits_low) | k;
       out_val[o] = (unsigned)p;
     }
-}
-
-// ---------------------------------------------------------------- radix sort
-//
-// LSD radix sort of the pairs, 8 bits per pass.  A block owns kSortTile
-// consecutive items, read in rounds of kSortThreads (round r, thread t holds
-// item r * kSortThreads + t), so the order of (round, thread) is the input
-// order and the scatter below keeps it among equal digits (stable).
-
-// Digit counts of each block's items (hist[digit * nblk + block]).
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long long* __restrict__ keys,
-                                                             long long n, int shift,
-                                                             unsigned* __restrict__ hist, int nblk) {
-  __shared__ unsigned h[kRadix];
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) h[d] = 0;
-  __syncthreads();
-  const long long base = (long long)blockIdx.x * kSortTile;
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const long long i = base + (long long)r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & (kRadix - 1)], 1u);
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d * nblk + blockIdx.x] = h[d];
-}
-
-// Stable scatter: item goes to scanned_hist[digit][block] + (items of this
-// block before it with the same digit).  Per round, lanes with equal digits
-// are ranked inside their warp (match), and warps are ranked per digit
-// through shared counts.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
-    const unsigned long long* __restrict__ kin, const unsigned* __restrict__ vin,
-    unsigned long long* __restrict__ kout, unsigned* __restrict__ vout, long long n, int shift,
-    const unsigned* __restrict__ hoff, int nblk) {
-  constexpr int kWarps = kSortThreads / 32;
-  __shared__ unsigned s_base[kRadix];          // running count per digit (earlier rounds)
-  __shared__ unsigned s_warp[kWarps][kRadix];  // this round: count, then exclusive prefix
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
-    s_base[d] = hoff[d * nblk + blockIdx.x];
-  const long long base = (long long)blockIdx.x * kSortTile;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int r = 0; r < kSortItems; ++r) {
-    const long long i = base + (long long)r * kSortThreads + threadIdx.x;
-    const bool ok = i < n;
-    unsigned long long key = 0;
-    unsigned val = 0;
-    if (ok) {
-      key = kin[i];
-      val = vin[i];
-    }
-    const unsigned d = ok ? (unsigned)(key >> shift) & (kRadix - 1) : (unsigned)kRadix;
-    __syncthreads();  // the previous round's prefixes have been read
-    for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) (&s_warp[0][0])[k] = 0;
-    __syncthreads();
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const unsigned rank = __popc(peers & lt);
-    if (ok && rank == 0) s_warp[wid][d] = __popc(peers);
-    __syncthreads();
-    for (int dd = threadIdx.x; dd < kRadix; dd += kSortThreads) {
-      unsigned run = s_base[dd];
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        const unsigned c = s_warp[w][dd];
-        s_warp[w][dd] = run;
-        run += c;
-      }
-      s_base[dd] = run;
-    }
-    __syncthreads();
-    if (ok) {
-      const unsigned pos = s_warp[wid][d] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
-    }
-  }
 }
 
 __global__ void __launch_bounds__(256) k_tile_ranges(const unsigned long long* __restrict__ keys,
@@ -491,7 +412,6 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     return SALF_ERR_INVALID;
   }
   const int key_bits = low_bits + tile_bits;
-  const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
 
   // per-voxel workspace
   const long long nn = std::max(n, 1LL);
@@ -614,23 +534,9 @@ salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double f
     k_emit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(count, rect, vkey, offs, (int)n, tiles_x,
                                                           low_bits, kA, vA);
     ++launches;
-    unsigned long long *ki = kA, *ko = kB;
-    unsigned *vi = vA, *vo = vB;
-    for (int pass = 0; pass < passes; ++pass) {
-      const int shift = kRadixBits * pass;
-      k_radix_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(ki, (long long)P, shift, hist,
-                                                            (int)nblk);
-      if ((e = scan_exclusive<unsigned, unsigned>(hist, hn, hoff, htmp, st, &launches)) !=
-          cudaSuccess)
-        return salf_cuda_fail(e, "raster sort scan");
-      k_radix_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(ki, vi, ko, vo, (long long)P, shift,
-                                                               hoff, (int)nblk);
-      launches += 2;
-      std::swap(ki, ko);
-      std::swap(vi, vo);
-    }
-    keys = ki;
-    vals = vi;
+    if ((e = radix_sort_pairs(kA, vA, kB, vB, (long long)P, key_bits, hist, hoff, htmp, st,
+                              &launches, &keys, &vals)) != cudaSuccess)
+      return salf_cuda_fail(e, "raster sort");
     k_tile_ranges<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(keys, (long long)P, low_bits,
                                                                ranges);
     ++launches;

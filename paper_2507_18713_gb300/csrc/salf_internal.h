@@ -203,6 +203,10 @@ struct salf_scene {
 void salf_set_error(const std::string& msg);
 salf_status salf_cuda_fail(cudaError_t e, const char* what);
 salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_scene** out);
+// The same build from device-resident level / ijk / params (validated by the caller).
+salf_status salf_build_scene_gpu(salf_ctx* ctx, const salf_scene_desc* d, salf_scene** out);
+// A device buffer owned (and freed) by the scene.
+salf_status salf_scene_dalloc(salf_scene* s, size_t bytes, void** p);
 salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* sen,
                                  const salf_render_opts* opts, ReqDev* r);
 int64_t salf_request_rays(const salf_sensor* sen);

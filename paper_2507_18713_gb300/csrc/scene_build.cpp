@@ -70,6 +70,8 @@ salf_status upload(salf_scene* s, const std::vector<T>& v, T** out) {
 
 }  // namespace
 
+salf_status salf_scene_dalloc(salf_scene* s, size_t bytes, void** p) { return dalloc(s, bytes, p); }
+
 salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_scene** out) {
   if (!ctx || !d || !out) {
     salf_set_error("salf_build_scene: null argument");
@@ -97,6 +99,13 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
   if (n > 0 && (reinterpret_cast<uintptr_t>(d->params) & 15u)) {
     salf_set_error("salf_build_scene: params must be 16-byte aligned");
     return SALF_ERR_INVALID;
+  }
+  if (d->keys_on_device) {
+    if (!d->params_on_device && n > 0) {
+      salf_set_error("salf_build_scene: keys_on_device needs params_on_device");
+      return SALF_ERR_INVALID;
+    }
+    return salf_build_scene_gpu(ctx, d, out);
   }
   cudaError_t ce = cudaSetDevice(ctx->device);
   if (ce != cudaSuccess) return salf_cuda_fail(ce, "cudaSetDevice");

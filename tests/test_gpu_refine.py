@@ -63,7 +63,7 @@ def test_refined_voxel_list_matches_oracle(salf, oracle_lib, seed, K):
     assert counts == dict(n_new=len(lv), n_kept=int((act == 0).sum()),
                           n_split=int((act == 1).sum()), n_pruned=int((act == 2).sum()))
     assert counts["n_split"] > 5 and counts["n_pruned"] > 5
-    assert np.array_equal(vs.level, lv) and np.array_equal(vs.ijk, ij)
+    assert np.array_equal(to_np(vs.level), lv) and np.array_equal(to_np(vs.ijk), ij)
     p = to_np(vs.params).astype(np.float64)
     assert np.abs(p - pr).max() <= 1e-5 * max(1.0, np.abs(pr).max())
     # the refined scene builds and renders like the oracle's refined voxel set
@@ -88,7 +88,8 @@ def test_refine_edge_cases(salf):
     ones = torch.ones(n, device="cuda")
     # nothing to do
     vs, c = g.refine(params, torch.zeros((n, 32), device="cuda"), ones, 1.0, 0.0)
-    assert c["n_new"] == n and np.array_equal(vs.level, sc.level) and np.array_equal(vs.ijk, sc.ijk)
+    assert c["n_new"] == n and np.array_equal(to_np(vs.level), sc.level)
+    assert np.array_equal(to_np(vs.ijk), sc.ijk)
     assert torch.equal(vs.params, params)
     # everything pruned
     vs, c = g.refine(params, big, ones, 1.0, 2.0)
