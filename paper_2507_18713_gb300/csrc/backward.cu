@@ -12,8 +12,9 @@
 //  d sigma / d b = -a s e^{-|s|/b} / (2 b^2)) and Eq. 2 (d c / d z = c (1 - c),
 // d z / d W_c = x, d z / d W_sh = gamma).  Gradients go to the caller's
 // input-order FP32 buffer with 16-byte vector atomics; lanes of a warp that
-// hit the same voxel in the same round first sum their rows in shared memory,
-// so each voxel takes one set of atomics per warp and round.
+// hit the same voxel in the same round stage their rows in shared memory and
+// share the summing: each adds some of the 16-byte chunks over the group, so
+// each voxel takes one set of atomics per warp and round.
 #include "traverse.cuh"
 
 using namespace salf;
@@ -122,30 +123,34 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ Launch
       }
       const int key = __ldg(&S.order[h.vox]);
       const unsigned peers = __match_any_sync(hit_lanes, key);
-      const int leader = __ffs(peers) - 1;
       const int nq = want_int ? 8 : 7;
-      if (peers != (1u << lane)) {
-        // several lanes hit this voxel: the lowest one sums their rows
-#pragma unroll
-        for (int q = 0; q < 32; ++q) rows[lane][q] = gr[q];
-        __syncwarp(peers);
-        if (lane == leader) {
-          unsigned rest = peers & (peers - 1u);
-          while (rest) {
-            const int l2 = __ffs(rest) - 1;
-            rest &= rest - 1u;
-#pragma unroll
-            for (int q = 0; q < 32; ++q) gr[q] += rows[l2][q];
-          }
-        }
-        __syncwarp(peers);
-      }
-      if (lane == leader) {
-        float4* dst = reinterpret_cast<float4*>(Q.d_params) + (size_t)key * 8;
+      float4* dst = reinterpret_cast<float4*>(Q.d_params) + (size_t)key * 8;
+      if (peers == (1u << lane)) {
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           if (q < nq)
             atomicAdd(dst + q, make_float4(gr[4 * q], gr[4 * q + 1], gr[4 * q + 2], gr[4 * q + 3]));
+      } else {
+        // several lanes hit this voxel: each sums some 16-byte chunks over the
+        // group's rows and adds them
+#pragma unroll
+        for (int q = 0; q < 32; ++q) rows[lane][q] = gr[q];
+        __syncwarp(peers);
+        const int g = __popc(peers), rank = __popc(peers & ((1u << lane) - 1u));
+        for (int c = rank; c < nq; c += g) {
+          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+          unsigned m = peers;
+          while (m) {
+            const int l2 = __ffs(m) - 1;
+            m &= m - 1u;
+            sum.x += rows[l2][4 * c];
+            sum.y += rows[l2][4 * c + 1];
+            sum.z += rows[l2][4 * c + 2];
+            sum.w += rows[l2][4 * c + 3];
+          }
+          atomicAdd(dst + c, sum);
+        }
+        __syncwarp(peers);
       }
       T = Tn;
       if (++k >= nv) w.alive = false;
