@@ -149,12 +149,22 @@ typedef struct {
  * want_intensity: also evaluate the intensity field.  visits_cap > 0 records,
  * per ray, the first visits_cap composited voxels (input indices, -1 padded)
  * and the total count: a debugging aid that slows the kernel.
+ * ray_segments: 1, 2, 4 or 8 splits each ray's span inside the voxels' box
+ * into that many equal parts walked at the same time by neighbouring threads
+ * and composited front to back in order (Eq. 3-4 are associative over
+ * consecutive spans); a part in which the ray actually stopped is walked
+ * again from the transmittance in front of it, so the outputs are those of
+ * the whole-ray walk up to rounding.  It shortens the longest rays' serial
+ * latency (LiDAR beams near the horizon).  0 = the library's choice per
+ * sensor kind.  Renders that record visits, ray dumps, step counts or alpha
+ * maxima, rasterised and actor renders and the backward pass walk whole rays.
  */
 typedef struct {
   float t_min_transmittance;
   float background[3];
   int32_t want_intensity;
   int32_t visits_cap;
+  int32_t ray_segments;
 } salf_render_opts;
 
 /*

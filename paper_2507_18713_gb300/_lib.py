@@ -42,7 +42,7 @@ class Sensor(C.Structure):
 
 class RenderOpts(C.Structure):
     _fields_ = [("t_min_transmittance", c_float), ("background", c_float * 3),
-                ("want_intensity", c_int32), ("visits_cap", c_int32)]
+                ("want_intensity", c_int32), ("visits_cap", c_int32), ("ray_segments", c_int32)]
 
 
 class Outputs(C.Structure):

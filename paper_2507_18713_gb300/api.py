@@ -69,12 +69,13 @@ def sensor_struct(sensor: dict, keep: list) -> L.Sensor:
 
 
 def opts_struct(t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
-                visits_cap=0) -> L.RenderOpts:
+                visits_cap=0, ray_segments=0) -> L.RenderOpts:
     o = L.RenderOpts()
     o.t_min_transmittance = float(t_min)
     o.background[:] = [float(v) for v in background]
     o.want_intensity = int(bool(want_intensity))
     o.visits_cap = int(visits_cap)
+    o.ray_segments = int(ray_segments)
     return o
 
 
@@ -178,11 +179,12 @@ class Scene:
     def render(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
                visits_cap=0, outputs=("rgb", "depth", "opacity"), saved=False, valid=True,
                stream=None, out: dict | None = None, ray_dump: bool = False,
-               steps: bool = False, max_alpha=None) -> dict:
+               steps: bool = False, max_alpha=None, ray_segments: int = 0) -> dict:
         """salf_render_rays into (new or given) CUDA tensors; asynchronous on
         `stream` (default: torch's current stream).  `max_alpha` (n float32 CUDA
         tensor, input order) is max-accumulated with each voxel's largest
-        composited alpha."""
+        composited alpha.  `ray_segments`: spans per ray walked in parallel
+        (0 = the library's choice, 1 = whole rays)."""
         R = n_rays(sensor)
         dev = torch.device("cuda", self.ctx.device)
         res = {} if out is None else dict(out)
@@ -211,7 +213,7 @@ class Scene:
             o.max_alpha = max_alpha.data_ptr()
         keep: list = []
         s = sensor_struct(sensor, keep)
-        op = opts_struct(t_min, background, want_intensity, visits_cap)
+        op = opts_struct(t_min, background, want_intensity, visits_cap, ray_segments)
         L.check(L.load().salf_render_rays(self._h, C.byref(s), C.byref(op), C.byref(o),
                                           _stream_ptr(stream)), "salf_render_rays")
         if keep:
@@ -339,7 +341,7 @@ class Scene:
 
     def render_host(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
                     want_intensity=False, outputs=("rgb", "depth", "opacity"), out=None,
-                    stream=None) -> dict:
+                    stream=None, ray_segments: int = 0) -> dict:
         """salf_render_rays with host output buffers (on_host = 1): synchronous,
         results land in (pinned, if given) host memory."""
         R = n_rays(sensor)
@@ -352,14 +354,14 @@ class Scene:
         o.on_host = 1
         keep: list = []
         s = sensor_struct(sensor, keep)
-        op = opts_struct(t_min, background, want_intensity, 0)
+        op = opts_struct(t_min, background, want_intensity, 0, ray_segments)
         L.check(L.load().salf_render_rays(self._h, C.byref(s), C.byref(op), C.byref(o),
                                           _stream_ptr(stream)), "salf_render_rays(host)")
         return res
 
     def render_host_noalloc(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
                             want_intensity=False, outputs=("rgb", "depth", "opacity"), out=None,
-                            stream=None) -> dict:
+                            stream=None, ray_segments: int = 0) -> dict:
         """salf_render_rays_host_noalloc: like render_host, but the library
         stages the outputs in its fixed device array instead of allocating."""
         R = n_rays(sensor)
@@ -372,7 +374,7 @@ class Scene:
             setattr(o, k, v.data_ptr())
         keep: list = []
         s = sensor_struct(sensor, keep)
-        op = opts_struct(t_min, background, want_intensity, 0)
+        op = opts_struct(t_min, background, want_intensity, 0, ray_segments)
         L.check(L.load().salf_render_rays_host_noalloc(self._h, C.byref(s), C.byref(op),
                                                        C.byref(o), _stream_ptr(stream)),
                 "salf_render_rays_host_noalloc")
@@ -437,10 +439,10 @@ class Server:
         self._sensors: dict = {}
 
     def submit(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
-               want_intensity=False) -> int:
+               want_intensity=False, ray_segments: int = 0) -> int:
         keep: list = []
         s = sensor_struct(sensor, keep)
-        op = opts_struct(t_min, background, want_intensity, 0)
+        op = opts_struct(t_min, background, want_intensity, 0, ray_segments)
         t = C.c_uint64()
         L.check(L.load().salf_serve_submit(self._h, C.byref(s), C.byref(op), C.byref(t)),
                 "salf_serve_submit")

@@ -17,11 +17,20 @@
 // each voxel takes one set of atomics per warp and round.
 #include "traverse.cuh"
 
+// warps per block and resident blocks per SM asked of the compiler
+#ifndef SALF_BWD_WARPS
+#define SALF_BWD_WARPS 8
+#endif
+#ifndef SALF_BWD_MIN_BLOCKS
+#define SALF_BWD_MIN_BLOCKS 1
+#endif
+
 using namespace salf;
 
 template <int DT, int MODE>
-__global__ void __launch_bounds__(256) k_backward(const __grid_constant__ LaunchParams P) {
-  const int warp = blockIdx.x * SALF_WARPS_PER_BLOCK + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
+    k_backward(const __grid_constant__ LaunchParams P) {
+  const int warp = blockIdx.x * SALF_BWD_WARPS + (threadIdx.x >> 5);
   if (warp >= P.total_tiles) return;
   const int lane = threadIdx.x & 31;
   const ReqDev& Q = P.req[find_request(P, warp)];
@@ -66,7 +75,7 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ Launch
   const float gbg = g[0] * Q.bg[0] + g[1] * Q.bg[1] + g[2] * Q.bg[2];
   float T = 1.f, Pk = 0.f;
   int k = 0;
-  __shared__ float s_rows[SALF_WARPS_PER_BLOCK][32][33];  // padded: conflict-free columns
+  __shared__ float s_rows[SALF_BWD_WARPS][32][33];  // padded: conflict-free columns
   float(*rows)[33] = s_rows[threadIdx.x >> 5];
 
   const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
@@ -160,9 +169,9 @@ __global__ void __launch_bounds__(256) k_backward(const __grid_constant__ Launch
 
 template <int DT, int MODE>
 static cudaError_t launch_bm(const LaunchParams& P, cudaStream_t st) {
-  const int blocks = (P.total_tiles + SALF_WARPS_PER_BLOCK - 1) / SALF_WARPS_PER_BLOCK;
+  const int blocks = (P.total_tiles + SALF_BWD_WARPS - 1) / SALF_BWD_WARPS;
   if (blocks == 0) return cudaSuccess;
-  k_backward<DT, MODE><<<blocks, 32 * SALF_WARPS_PER_BLOCK, 0, st>>>(P);
+  k_backward<DT, MODE><<<blocks, 32 * SALF_BWD_WARPS, 0, st>>>(P);
   return cudaGetLastError();
 }
 

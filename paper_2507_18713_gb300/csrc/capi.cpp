@@ -345,6 +345,26 @@ salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* s,
   for (int k = 0; k < 3; ++k) r->bg[k] = o->background[k];
   r->want_int = o->want_intensity ? 1 : 0;
   r->vcap = o->visits_cap;
+  int segs = o->ray_segments;
+  if (segs == 0) segs = o->visits_cap > 0 ? 1 : salf_auto_segments(s->kind);
+  if (segs != 1 && segs != 2 && segs != 4 && segs != 8) {
+    g_err = "options: ray_segments must be 0, 1, 2, 4 or 8";
+    return SALF_ERR_INVALID;
+  }
+  salf_request_tiling(r, s, o->visits_cap > 0 ? 0 : __builtin_ctz((unsigned)segs));
+  return SALF_OK;
+}
+
+int salf_auto_segments(int kind) {
+  switch (kind) {
+    case SALF_LIDAR_SPIN: return SALF_SEGMENTS_LIDAR;
+    case SALF_FISHEYE_EQUIDIST: return SALF_SEGMENTS_FISHEYE;
+    case SALF_PANO_EQUIRECT: return SALF_SEGMENTS_PANORAMA;
+    default: return 1;
+  }
+}
+
+void salf_request_tiling(ReqDev* r, const salf_sensor* s, int seg_shift) {
   if (s->kind == SALF_RAYS_EXPLICIT || s->height == 1) {
     r->tile_w = 32;
     r->tile_h = 1;
@@ -356,11 +376,22 @@ salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* s,
     r->tile_w = SALF_TILE_W;
     r->tile_h = SALF_TILE_H;
   }
+  // a warp holds 32 >> seg_shift rays: fewer columns first, then fewer rows
+  for (int k = 0; k < seg_shift; ++k) {
+    if (r->tile_w > 1)
+      r->tile_w >>= 1;
+    else
+      r->tile_h >>= 1;
+  }
+  if (s->kind == SALF_LIDAR_SPIN && seg_shift > 0 && s->height > 1) {
+    r->tile_w = std::min(SALF_SEG_LIDAR_TILE_W, 32 >> seg_shift);
+    r->tile_h = (32 >> seg_shift) / r->tile_w;
+  }
+  r->seg_shift = seg_shift;
   r->tiles_x = (s->width + r->tile_w - 1) / r->tile_w;
   r->tiles_y = (s->height + r->tile_h - 1) / r->tile_h;
   r->n_tiles = r->tiles_x * r->tiles_y;
   r->first_row = horizon_tile_row(s, r->tile_h, r->tiles_y);
-  return SALF_OK;
 }
 
 static salf_render_opts default_opts() {
@@ -408,6 +439,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
   ReqDev& r = P.req[0];
   salf_status st = salf_prepare_request(sc, sen, &o, &r);
   if (st != SALF_OK) return st;
+  if (out->ray_dump || out->steps || out->max_alpha) salf_request_tiling(&r, sen, 0);
   P.total_tiles = r.n_tiles;
   P.step_budget = salf_step_budget();
   const size_t R = (size_t)salf_request_rays(sen);
@@ -524,6 +556,7 @@ extern "C" salf_status salf_render_raster(salf_scene* sc, const salf_sensor* sen
   ReqDev r;
   salf_status st = salf_prepare_request(sc, sen, &o, &r);
   if (st != SALF_OK) return st;
+  salf_request_tiling(&r, sen, 0);  // this path walks whole rays
   r.rgb = out->rgb;
   r.depth = out->depth;
   r.opacity = out->opacity;
@@ -656,6 +689,7 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
   ReqDev& r = P.req[0];
   salf_status st = salf_prepare_request(sc, sen, &o, &r);
   if (st != SALF_OK) return st;
+  salf_request_tiling(&r, sen, 0);  // this path walks whole rays
   P.total_tiles = r.n_tiles;
   P.step_budget = salf_step_budget();
   r.rgb = out->rgb;
@@ -815,6 +849,7 @@ extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* s
   ReqDev& r = P.req[0];
   salf_status st = salf_prepare_request(sc, sen, &o, &r);
   if (st != SALF_OK) return st;
+  salf_request_tiling(&r, sen, 0);  // this path walks whole rays
   r.vcap = 0;
   r.bsaved = saved;
   r.g_rgb = d_rgb;

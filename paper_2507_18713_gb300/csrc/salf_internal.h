@@ -19,6 +19,21 @@
 #endif
 #define SALF_TILE_H (32 / SALF_TILE_W)
 #define SALF_WARPS_PER_BLOCK 8
+// Spans per ray when the caller leaves the choice to the library (power of 2 <= 8).
+#ifndef SALF_SEGMENTS_LIDAR
+#define SALF_SEGMENTS_LIDAR 4
+#endif
+#ifndef SALF_SEGMENTS_FISHEYE
+#define SALF_SEGMENTS_FISHEYE 1
+#endif
+#ifndef SALF_SEGMENTS_PANORAMA
+#define SALF_SEGMENTS_PANORAMA 1
+#endif
+// Azimuths per warp tile of a LiDAR walked in spans (power of 2; the rest of
+// the tile's rays are beams).
+#ifndef SALF_SEG_LIDAR_TILE_W
+#define SALF_SEG_LIDAR_TILE_W 8
+#endif
 
 // Device status-word bits.
 #define SALF_DEVERR_STEP_CAP 1  // a traversal loop reached its iteration bound
@@ -112,9 +127,12 @@ struct ReqDev {
   // tiling: tile rows are launched outward from first_row, alternating below
   // and above it (the most nearly horizontal rays, the longest ones, first)
   int tiles_x, tiles_y;
-  int tile_w, tile_h;
+  int tile_w, tile_h;  // rays per warp tile: tile_w x tile_h = 32 >> seg_shift
   int tile_begin, n_tiles;
   int first_row;
+  // each ray's span in the voxels' box is cut into 2^seg_shift equal parts,
+  // walked by neighbouring lanes and composited in order (forward only)
+  int seg_shift;
   // optional subset of the tiles (device): warp w of the request renders
   // tile tile_list[w] while w < *tile_count (null: every tile, in order)
   const int* tile_list;
@@ -209,6 +227,10 @@ salf_status salf_build_scene_gpu(salf_ctx* ctx, const salf_scene_desc* d, salf_s
 salf_status salf_scene_dalloc(salf_scene* s, size_t bytes, void** p);
 salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* sen,
                                  const salf_render_opts* opts, ReqDev* r);
+// Warp tiles of a request with 2^seg_shift lanes per ray (0: whole rays);
+// callers whose kernels walk whole rays re-tile with 0.
+void salf_request_tiling(ReqDev* r, const salf_sensor* s, int seg_shift);
+int salf_auto_segments(int kind);
 int64_t salf_request_rays(const salf_sensor* sen);
 void salf_relative_rotation(const double* pose0, const double* pose1, float axis[3],
                             float* angle);

@@ -154,6 +154,19 @@ struct Walk {
   bool alive;
 };
 
+// (Re)start a walk at distance t: the cell holding the point there, kept
+// inside the tight box of the voxels.
+__device__ __forceinline__ void walk_seek(const DevScene& S, Walk& w, float t) {
+  w.t = t;
+  w.steps = 0;
+  w.cl = min(S.CL - 1, 6);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int q = w.Oi[a] + __float2int_rd(fmaf(t, w.D[a], w.Of[a]));
+    w.c[a] = min(max(q, S.bmin[a]), max(S.bmax[a] - 1, S.bmin[a]));
+  }
+}
+
 __device__ __forceinline__ void walk_init(const DevScene& S, const Ray& r, Walk& w) {
   float isf = (float)S.inv_sfin;
   float t0 = r.tn, t1 = r.tf;
@@ -172,15 +185,8 @@ __device__ __forceinline__ void walk_init(const DevScene& S, const Ray& r, Walk&
     t1 = fminf(t1, fmaxf(lo, hi));
   }
   w.alive = r.valid && (t0 < t1);
-  w.t = t0;
   w.tend = t1;
-  w.steps = 0;
-  w.cl = min(S.CL - 1, 6);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    int q = r.Oi[a] + __float2int_rd(fmaf(t0, w.D[a], r.Of[a]));
-    w.c[a] = min(max(q, S.bmin[a]), max(S.bmax[a] - 1, S.bmin[a]));
-  }
+  walk_seek(S, w, t0);
 }
 
 __device__ __forceinline__ void prefetch_l1(const void* p) {
@@ -332,6 +338,20 @@ struct Hit {
   int ls;
   float tin, tout;
 };
+
+// Distance at which the ray enters a hit's box, not before t0 (where its walk
+// from the start began): the same formula as the entry next_hit reports, but
+// independent of where a walk started, so every walk of one ray agrees on it.
+__device__ __forceinline__ float hit_entry(const Walk& w, const Hit& h, float t0) {
+  const int E = 1 << h.ls;
+  float t = t0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int p = (w.D[a] > 0.f ? h.base[a] : h.base[a] + E) - w.Oi[a];
+    t = fmaxf(t, ((float)p - w.Of[a]) * w.invD[a]);
+  }
+  return t;
+}
 
 // Leave the box [lo, hi) through its face on `axis` at distance te: the next
 // point to locate is the neighbour cell across that face, the other
