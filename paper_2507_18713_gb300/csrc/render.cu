@@ -238,7 +238,7 @@ static cudaError_t launch_fm(const LaunchParams& P, bool dump, bool coherent, bo
   return cudaGetLastError();
 }
 
-cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
+static cudaError_t launch_variant(const LaunchParams& P, cudaStream_t st) {
   bool dump = false, coherent = true, seg = false;
   for (int i = 0; i < P.n_req; ++i) {
     const ReqDev& q = P.req[i];
@@ -256,4 +256,28 @@ cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
   if (dt == SALF_BF16 && md == SALF_FIELD_EXP)
     return launch_fm<SALF_BF16, SALF_FIELD_EXP>(P, dump, coherent, seg, st);
   return launch_fm<SALF_BF16, SALF_FIELD_SDF>(P, dump, coherent, seg, st);
+}
+
+// A batch that mixes span-parallel requests with whole-ray ones runs as two
+// launches (one per variant), so the whole-ray requests keep their own
+// variant's shape; each request's result does not depend on the split.
+cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
+  int n_seg = 0;
+  for (int i = 0; i < P.n_req; ++i) n_seg += P.req[i].seg_shift > 0;
+  if (n_seg == 0 || n_seg == P.n_req || P.req[0].tile_list) return launch_variant(P, st);
+  for (int part = 0; part < 2; ++part) {
+    LaunchParams G = P;
+    G.n_req = 0;
+    G.total_tiles = 0;
+    for (int i = 0; i < P.n_req; ++i) {
+      if ((P.req[i].seg_shift > 0) != (part == 0)) continue;
+      G.req[G.n_req] = P.req[i];
+      G.req[G.n_req].tile_begin = G.total_tiles;
+      G.total_tiles += P.req[i].n_tiles;
+      ++G.n_req;
+    }
+    const cudaError_t e = launch_variant(G, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
