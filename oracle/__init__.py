@@ -16,6 +16,8 @@ from .oracle import (  # noqa: F401
     subdivide_record,
     face_pairs,
     reg_loss,
+    secondary_rays,
+    voxel_at,
     backward,
     gen_rays,
     trace,

@@ -123,6 +123,10 @@ class OracleScene:
         self._params = np.ascontiguousarray(p, dtype=np.float64)
         self.n = int(self._level.shape[0])
         self.mode = scene.mode
+        self.origin = np.asarray(scene.origin, dtype=np.float64)
+        self.s0 = float(scene.s0)
+        self.dims = tuple(int(v) for v in scene.dims)
+        self.max_level = int(scene.max_level)
         d = _SceneDesc()
         d.n = self.n
         d.origin[:] = [float(v) for v in scene.origin]
@@ -345,6 +349,72 @@ def render_actors(oscene, actors, sensor, idx=None, t_min=1e-4, background=(0.0,
     del keep
     res["valid"] = res["valid"].astype(bool)
     return res
+
+
+def voxel_at(oscene, X) -> int:
+    """Index of the voxel whose box [lo, lo + edge) holds the point X (world
+    metres), else -1.  The voxels are disjoint (Sec. III-D), so the cell
+    holding X is looked up at each level and at most one level matches."""
+    X = np.asarray(X, dtype=np.float64)
+    for lev in range(oscene.max_level + 1):
+        e = oscene.s0 / (1 << lev)
+        c = np.floor((X - oscene.origin) / e).astype(np.int64)
+        if (c < 0).any() or (c >= np.asarray(oscene.dims, np.int64) << lev).any():
+            return -1
+        v = oscene.lookup(lev, int(c[0]), int(c[1]), int(c[2]))
+        if v >= 0:
+            return v
+    return -1
+
+
+def secondary_rays(oscene, sensor, depth, opacity, kind="reflect", eta=1.0 / 1.33,
+                   light_dir=(0.0, 0.0, 1.0), min_opacity=0.5, offset=1e-3, t_far=0.0, idx=None):
+    """Secondary rays at the expected hit point of a render (Sec. V-C and
+    Fig. 1 name reflection, refraction and shadows; the paper gives no
+    construction, so this follows the library's stated one), in FP64:
+    X = o + (D / O) d for rays with O >= min_opacity; the voxel holding X; its
+    outward normal n = -W[0:3] / |W[0:3]|, turned so that n . d <= 0; then the
+    mirror direction d - 2 (d . n) n, Snell's refraction with ratio eta (total
+    internal reflection falls back to the mirror direction), or the unit light
+    direction.  Rows (origin, direction, 0, t_far); no ray -> all zero."""
+    r = gen_rays(sensor, idx)
+    depth = np.asarray(depth, dtype=np.float64).ravel()
+    opacity = np.asarray(opacity, dtype=np.float64).ravel()
+    light = np.asarray(light_dir, dtype=np.float64)
+    light = light / np.linalg.norm(light)
+    out = np.zeros((len(r["o"]), 8))
+    for i in range(len(r["o"])):
+        O = opacity[i]
+        if not r["valid"][i] or not (O >= min_opacity and O > 0.0):
+            continue
+        d = r["d"][i]
+        X = r["o"][i] + (depth[i] / O) * d
+        v = voxel_at(oscene, X)
+        if v < 0:
+            continue
+        g = oscene._params[v, :3]
+        gn = np.linalg.norm(g)
+        if gn == 0.0:
+            continue
+        n = -g / gn
+        if n @ d > 0.0:
+            n = -n
+        dn = n @ d
+        side = 1.0
+        if kind == "shadow":
+            w = light
+        else:
+            c = -dn
+            k = 1.0 - eta * eta * (1.0 - c * c)
+            if kind == "refract" and k >= 0.0:
+                w = eta * d + (eta * c - np.sqrt(k)) * n
+                side = -1.0
+            else:
+                w = d - 2.0 * dn * n
+        out[i, :3] = X + side * offset * n
+        out[i, 3:6] = w
+        out[i, 7] = t_far if t_far > 0.0 else 0.0
+    return out
 
 
 def subdivide_record(record, child):
