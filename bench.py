@@ -656,6 +656,32 @@ def main():
                         note="raster time includes projection, tile lists, sort and the one "
                              "host wait for the list size", points=res)
 
+        def secondary_section():
+            # Sec. V-C / Fig. 1: reflection and shadow rays spawned at the 1080p
+            # frame's expected hit points, then traced through the same scene
+            R = cam["width"] * cam["height"]
+            prim = g.render(cam, outputs=("depth", "opacity"))
+            rays = torch.empty((R, 8), device="cuda")
+            o = {k: torch.empty((R, 3) if k == "rgb" else (R,), device="cuda")
+                 for k in ("rgb", "depth", "opacity")}
+            res = dict(workload="1080p pinhole frame of the driving scene; rays spawned where "
+                       "opacity >= 0.5; L2 flushed; median ms")
+            for kind, kw in (("reflect", {}), ("shadow", dict(light_dir=(0.4, 0.3, 1.0)))):
+                gen = lambda: g.secondary_rays(cam, prim["depth"], prim["opacity"], kind=kind,
+                                               out=rays, **kw)
+                ms_gen = timed_renders(torch, gen, 20, args.warmup, flush)
+                gen()
+                torch.cuda.synchronize()
+                spawned = int(rays[:, 3:6].abs().sum(dim=1).gt(0).sum().item())
+                sen = P.rays_sensor(rays)
+                tr = lambda: g.render(sen, outputs=("rgb", "depth", "opacity"), out=o, valid=False)
+                ms_tr = timed_renders(torch, tr, 20, args.warmup, flush)
+                t = statistics.median(ms_tr)
+                res[kind] = dict(spawned=spawned, generate_ms=statistics.median(ms_gen),
+                                 trace_ms=t, trace_mrays_s=spawned / (t * 1e-3) / 1e6)
+            g.check()
+            return res
+
         def actors_section():
             # Sec. IV-A: the same frames with 24 moving car-sized actors on the road
             tracks = synth.actor_tracks(24, seed=5)
@@ -687,6 +713,7 @@ def main():
         extra("lidar", lidar_section)
         extra("fisheye", fisheye_section)
         extra("raster_vs_ray", raster_section)
+        extra("secondary", secondary_section)
         extra("actors", actors_section)
         del g
         torch.cuda.empty_cache()

@@ -408,6 +408,51 @@ salf_status salf_scene_reg_loss(salf_scene* scene, const float* params, float la
                                 float lambda_alpha, float lambda_n, float* loss, float* grads,
                                 void* stream);
 
+/*
+ * Secondary rays (Sec. V-C and Fig. 1 name refraction, reflection and
+ * shadows among the effects ray casting through the voxels supports; the
+ * paper gives no construction, this is the library's).  For primary ray i of `sensor` (the
+ * sensor of an earlier salf_render_rays, same ray generation), with that
+ * render's depth D_i = sum w t_m and opacity O_i = sum w (device, R floats):
+ *   - no secondary ray (direction 0, an invalid explicit ray) unless the ray
+ *     is valid and O_i >= min_opacity;
+ *   - hit point X = o + (D_i / O_i) d, the expected termination distance;
+ *   - no secondary ray unless X lies inside a voxel whose geometry slopes
+ *     g = W[0:3] (record slots 0..2: W_sigma or W_s) are not all 0;
+ *   - surface normal n = -g / |g| (the field grows into the surface for
+ *     both Eq. 1 and Eq. 6), turned to face the incoming ray (n . d <= 0);
+ *   - REFLECT: r = d - 2 (d . n) n, origin X + offset n;
+ *     REFRACT (Snell, eta = n_incident / n_transmitted): with c = -d . n and
+ *     k = 1 - eta^2 (1 - c^2), r = eta d + (eta c - sqrt(k)) n, origin
+ *     X - offset n; k < 0 (total internal reflection) gives the reflection;
+ *     SHADOW: r = light_dir / |light_dir| (toward a distant light), origin
+ *     X + offset n.
+ * rays_out (R x 8 FP32, device, 16-byte aligned) gets (origin, r, 0, t_far),
+ * the salf_sensor explicit-ray layout: render them with SALF_RAYS_EXPLICIT
+ * (their opacity is the shadow's occlusion; their colour the reflected or
+ * refracted light).  Asynchronous on `stream`.  Errors: INVALID (null or
+ * misaligned pointers, kind, eta <= 0, zero light direction, min_opacity
+ * outside (0, 1], offset < 0), CUDA.
+ */
+typedef enum {
+  SALF_SECONDARY_REFLECT = 0,
+  SALF_SECONDARY_REFRACT = 1,
+  SALF_SECONDARY_SHADOW = 2
+} salf_secondary_kind;
+
+typedef struct {
+  int32_t kind;
+  float eta;
+  float light_dir[3];
+  float min_opacity;
+  float offset;  /* metres */
+  float t_far;   /* secondary ray length; <= 0: unbounded */
+} salf_secondary_opts;
+
+salf_status salf_secondary_rays(salf_scene* scene, const salf_sensor* sensor, const float* depth,
+                                const float* opacity, const salf_secondary_opts* opts,
+                                float* rays_out, void* stream);
+
 /* Check the scene's device status word (synchronises the device).  Returns
  * SALF_ERR_DEVICE if a kernel hit an internal bound since the last check. */
 salf_status salf_scene_check(salf_scene* scene);

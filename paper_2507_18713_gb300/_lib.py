@@ -74,6 +74,14 @@ class RefineCounts(C.Structure):
                 ("n_pruned", c_int64)]
 
 
+class SecondaryOpts(C.Structure):
+    _fields_ = [("kind", c_int32), ("eta", c_float), ("light_dir", c_float * 3),
+                ("min_opacity", c_float), ("offset", c_float), ("t_far", c_float)]
+
+
+SECONDARY = {"reflect": 0, "refract": 1, "shadow": 2}
+
+
 class RasterStats(C.Structure):
     _fields_ = [("visible_voxels", c_int64), ("pairs", c_int64), ("tiles", c_int32),
                 ("key_bits", c_int32), ("kernels", c_int32), ("reserved", c_int32)]
@@ -97,6 +105,8 @@ SIGNATURES = {
                                 c_int32),
     "salf_scene_reg_loss": ([c_void_p, c_void_p, C.c_float, C.c_float, C.c_float, c_void_p,
                              c_void_p, c_void_p], c_int32),
+    "salf_secondary_rays": ([c_void_p, C.POINTER(Sensor), c_void_p, c_void_p,
+                             C.POINTER(SecondaryOpts), c_void_p, c_void_p], c_int32),
     "salf_render_raster": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),
                             C.POINTER(Outputs), C.POINTER(RasterStats), c_void_p], c_int32),
     "salf_render_rays_host_noalloc": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),

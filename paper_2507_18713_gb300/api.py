@@ -83,6 +83,15 @@ def n_rays(sensor: dict) -> int:
     return int(sensor["width"]) * int(sensor["height"])
 
 
+def rays_sensor(rays) -> dict:
+    """Explicit-ray sensor over an (R, 8) float32 CUDA tensor of rows
+    (origin, direction, t_near, t_far), e.g. from Scene.secondary_rays."""
+    R = int(rays.shape[0])
+    return dict(kind="explicit", width=R, height=1, fx=0.0, fy=0.0, cx=0.0, cy=0.0, fov=0.0,
+                elev_min=0.0, elev_max=0.0, pose0=np.eye(3, 4), pose1=np.eye(3, 4), t0=0.0,
+                t1=0.0, rolling_shutter=False, t_near=0.0, t_far=0.0, rays=rays)
+
+
 class VoxelSet:
     """A voxel set on a scene grid (what salf_build_scene takes): origin, s0,
     dims, max_level, level (n,), ijk (n, 3), params (n, 32), mode."""
@@ -299,6 +308,28 @@ class Scene:
                                              grads.data_ptr(), _stream_ptr(stream)),
                 "salf_scene_reg_loss")
         return loss, grads
+
+    def secondary_rays(self, sensor: dict, depth, opacity, kind="reflect", eta=1.0 / 1.33,
+                       light_dir=(0.0, 0.0, 1.0), min_opacity=0.5, offset=1e-3, t_far=0.0,
+                       out=None, stream=None):
+        """salf_secondary_rays: (R, 8) CUDA tensor of explicit rays spawned at
+        the expected hit points of a render of `sensor` (its depth and opacity
+        outputs).  Trace them with render(rays_sensor(rays))."""
+        R = n_rays(sensor)
+        dev = torch.device("cuda", self.ctx.device)
+        rays = out if out is not None else torch.empty((R, 8), dtype=torch.float32, device=dev)
+        o = L.SecondaryOpts()
+        o.kind = L.SECONDARY[kind]
+        o.eta = float(eta)
+        o.light_dir[:] = [float(v) for v in light_dir]
+        o.min_opacity, o.offset, o.t_far = float(min_opacity), float(offset), float(t_far)
+        keep: list = []
+        s = sensor_struct(sensor, keep)
+        depth, opacity = depth.contiguous(), opacity.contiguous()
+        L.check(L.load().salf_secondary_rays(self._h, C.byref(s), depth.data_ptr(),
+                                             opacity.data_ptr(), C.byref(o), rays.data_ptr(),
+                                             _stream_ptr(stream)), "salf_secondary_rays")
+        return rays
 
     def render_actors(self, sensor: dict, actors, t_min=1e-4, background=(0.0, 0.0, 0.0),
                       want_intensity=False, visits_cap=0, outputs=("rgb", "depth", "opacity"),
