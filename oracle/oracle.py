@@ -53,14 +53,15 @@ class _Sensor(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("t_min", C.c_double), ("background", C.c_double * 3),
-                ("want_intensity", C.c_int32), ("brute_force", C.c_int32)]
+                ("want_intensity", C.c_int32), ("brute_force", C.c_int32),
+                ("want_raydrop", C.c_int32)]
 
 
 class _Outputs(C.Structure):
     _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("opacity", C.c_void_p),
                 ("intensity", C.c_void_p), ("t_end", C.c_void_p), ("term_gap", C.c_void_p),
                 ("n_visits", C.c_void_p), ("valid", C.c_void_p), ("visits", C.c_void_p),
-                ("visits_cap", C.c_int32), ("max_alpha", C.c_void_p)]
+                ("visits_cap", C.c_int32), ("max_alpha", C.c_void_p), ("raydrop", C.c_void_p)]
 
 
 class _Actor(C.Structure):
@@ -95,7 +96,7 @@ def _load():
             lib.orc_render.argtypes = [vp, C.POINTER(_Sensor), C.POINTER(_Opts), vp, i64,
                                        C.POINTER(_Outputs)]
             lib.orc_backward.argtypes = [vp, C.POINTER(_Sensor), C.POINTER(_Opts), vp, i64, vp,
-                                         vp, vp, vp, vp]
+                                         vp, vp, vp, vp, vp]
             lib.orc_num_threads.restype = C.c_int
             lib.orc_subdivide_record.argtypes = [vp, i32, vp]
             lib.orc_render_actors.argtypes = [vp, vp, i32, C.POINTER(_Sensor), C.POINTER(_Opts),
@@ -180,12 +181,14 @@ def _sensor(s):
     return c, keep
 
 
-def _opts(t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False, brute_force=False):
+def _opts(t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False, brute_force=False,
+          want_raydrop=False):
     o = _Opts()
     o.t_min = float(t_min)
     o.background[:] = [float(v) for v in background]
     o.want_intensity = int(bool(want_intensity))
     o.brute_force = int(bool(brute_force))
+    o.want_raydrop = int(bool(want_raydrop))
     return o
 
 
@@ -264,10 +267,12 @@ def trace_eps(oscene, o, d, t_near, t_far, eps_abs, eps_rel, sign, cap=1 << 16,
 
 
 def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
-           want_intensity=False, brute_force=False, visits_cap=0, max_alpha=None):
+           want_intensity=False, brute_force=False, visits_cap=0, max_alpha=None,
+           want_raydrop=False):
     """Render the selected rays (all if idx is None) in FP64.  `max_alpha`
     (n float64, input order) is max-accumulated with each voxel's largest
-    composited alpha."""
+    composited alpha.  want_raydrop adds `raydrop`: sum of w * sigmoid(rho)
+    over the composited voxels (rho = record slot 31) plus T_end."""
     lib = _load()
     s, keep = _sensor(sensor)
     idx, m = _idx(sensor, idx)
@@ -284,7 +289,10 @@ def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
     if max_alpha is not None:
         assert max_alpha.dtype == np.float64 and max_alpha.flags.c_contiguous
         o.max_alpha = _ptr(max_alpha)
-    opt = _opts(t_min, background, want_intensity, brute_force)
+    if want_raydrop:
+        res["raydrop"] = np.zeros(m)
+        o.raydrop = _ptr(res["raydrop"])
+    opt = _opts(t_min, background, want_intensity, brute_force, want_raydrop)
     st = lib.orc_render(oscene._h, C.byref(s), C.byref(opt), _ptr(idx), m, C.byref(o))
     if st != 0:
         raise RuntimeError(f"oracle render failed: {st}")
@@ -295,7 +303,7 @@ def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
 
 def backward(oscene, sensor, g_rgb=None, g_depth=None, g_opacity=None, g_intensity=None,
              idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
-             brute_force=False):
+             brute_force=False, g_raydrop=None):
     """Gradient (n, 32) of sum(g . outputs) w.r.t. every record scalar."""
     lib = _load()
     s, keep = _sensor(sensor)
@@ -308,9 +316,10 @@ def backward(oscene, sensor, g_rgb=None, g_depth=None, g_opacity=None, g_intensi
         return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
 
     gr, gd, go, gi = arr(g_rgb, (m, 3)), arr(g_depth, (m,)), arr(g_opacity, (m,)), arr(g_intensity, (m,))
-    opt = _opts(t_min, background, want_intensity, brute_force)
+    gp = arr(g_raydrop, (m,))
+    opt = _opts(t_min, background, want_intensity, brute_force, g_raydrop is not None)
     st = lib.orc_backward(oscene._h, C.byref(s), C.byref(opt), _ptr(idx), m, _ptr(gr), _ptr(gd),
-                          _ptr(go), _ptr(gi), _ptr(grad))
+                          _ptr(go), _ptr(gi), _ptr(gp), _ptr(grad))
     if st != 0:
         raise RuntimeError(f"oracle backward failed: {st}")
     del keep

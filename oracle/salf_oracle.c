@@ -629,7 +629,7 @@ void orc_field(const double* rec, int32_t mode, const double x[3], const double 
 typedef struct {
   int64_t n;            /* composited voxels */
   int32_t* vox;
-  double *tm, *dl, *sig, *lin, *c, *io, *alpha, *T, *w, *x;
+  double *tm, *dl, *sig, *lin, *c, *io, *dr, *alpha, *T, *w, *x;
   double t_end, gap;
 } ray_record;
 
@@ -641,6 +641,7 @@ static void rr_free(ray_record* rr) {
   free(rr->lin);
   free(rr->c);
   free(rr->io);
+  free(rr->dr);
   free(rr->alpha);
   free(rr->T);
   free(rr->w);
@@ -662,6 +663,7 @@ static void composite_ray(const orc_scene* s, const orc_opts* opt, const double 
   rr->lin = (double*)malloc(M * sizeof(double));
   rr->c = (double*)malloc(3 * M * sizeof(double));
   rr->io = (double*)malloc(M * sizeof(double));
+  rr->dr = (double*)malloc(M * sizeof(double));
   rr->alpha = (double*)malloc(M * sizeof(double));
   rr->T = (double*)malloc(M * sizeof(double));
   rr->w = (double*)malloc(M * sizeof(double));
@@ -699,6 +701,9 @@ static void composite_ray(const orc_scene* s, const orc_opts* opt, const double 
       rr->x[3 * k + q] = x[q];
     }
     rr->io[k] = io;
+    /* raydrop field (paper silent on its form): a per-voxel logit, record
+     * slot 31, composited like intensity */
+    rr->dr[k] = opt->want_raydrop ? sigmoid(rec[31]) : 0.0;
     rr->alpha[k] = alpha;
     rr->T[k] = T;
     rr->w[k] = w;
@@ -727,7 +732,7 @@ int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
     double o[3], d[3], tn, tf, tau;
     uint8_t valid;
     one_ray(sen, r, o, d, &tn, &tf, &tau, &valid);
-    double C[3] = {0, 0, 0}, D = 0, O = 0, I = 0, Tend = 1.0, gap = INFINITY;
+    double C[3] = {0, 0, 0}, D = 0, O = 0, I = 0, P = 0, Tend = 1.0, gap = INFINITY;
     int64_t nv = 0;
     ray_record rr;
     memset(&rr, 0, sizeof(rr));
@@ -743,6 +748,7 @@ int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
         D += rr.w[k] * rr.tm[k];
         O += rr.w[k];
         I += rr.w[k] * rr.io[k];
+        P += rr.w[k] * rr.dr[k];
       }
       Tend = rr.t_end;
       gap = rr.gap;
@@ -754,6 +760,7 @@ int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
     if (out->depth) out->depth[i] = D;
     if (out->opacity) out->opacity[i] = O;
     if (out->intensity) out->intensity[i] = I;
+    if (out->raydrop) out->raydrop[i] = valid ? P + Tend : 0.0;
     if (out->t_end) out->t_end[i] = valid ? Tend : 1.0;
     if (out->term_gap) out->term_gap[i] = gap;
     if (out->n_visits) out->n_visits[i] = (int32_t)nv;
@@ -774,12 +781,16 @@ int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
   } while (0)
 
 /* Adjoint of Eq. 1-6 for L = sum_r g_r . outputs_r.  With q_k = (c_k, t_mid,k,
- * 1, iota_k) and w_k = T_k alpha_k, tau_k = sigma_k delta_k:
- *   dL/dtau_k = T_{k+1} (g . q_k) - sum_{j>k} w_j (g . q_j) - T_end (g_rgb . bg)
- * then the chain rule through Eq. 1/6 (density) and Eq. 2 (colour). */
+ * 1, iota_k, rho_k) (rho_k = sigmoid of the raydrop logit) and w_k = T_k alpha_k,
+ * tau_k = sigma_k delta_k:
+ *   dL/dtau_k = T_{k+1} (g . q_k) - sum_{j>k} w_j (g . q_j)
+ *               - T_end (g_rgb . bg + g_raydrop)
+ * (the raydrop output adds T_end like a background of 1), then the chain rule
+ * through Eq. 1/6 (density), Eq. 2 (colour) and the sigmoid fields. */
 int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
                  const int64_t* idx, int64_t m, const double* g_rgb, const double* g_depth,
-                 const double* g_opacity, const double* g_intensity, double* grad) {
+                 const double* g_opacity, const double* g_intensity, const double* g_raydrop,
+                 double* grad) {
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < m; ++i) {
     int64_t r = idx ? idx[i] : i;
@@ -793,6 +804,7 @@ int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
     if (g_depth) gd = g_depth[i];
     if (g_opacity) go = g_opacity[i];
     if (g_intensity && opt->want_intensity) gi = g_intensity[i];
+    double gp = (g_raydrop && opt->want_raydrop) ? g_raydrop[i] : 0.0;
     ray_record rr;
     memset(&rr, 0, sizeof(rr));
     composite_ray(s, opt, o, d, tn, tf, &rr);
@@ -801,14 +813,14 @@ int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
     double* suf = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
     for (int64_t k = 0; k < n; ++k)
       gq[k] = gc[0] * rr.c[3 * k] + gc[1] * rr.c[3 * k + 1] + gc[2] * rr.c[3 * k + 2] +
-              gd * rr.tm[k] + go + gi * rr.io[k];
+              gd * rr.tm[k] + go + gi * rr.io[k] + gp * rr.dr[k];
     double acc = 0;
     for (int64_t k = n - 1; k >= 0; --k) {
       suf[k] = acc; /* sum_{j>k} w_j gq_j */
       acc += rr.w[k] * gq[k];
     }
     double gbg = gc[0] * opt->background[0] + gc[1] * opt->background[1] +
-                 gc[2] * opt->background[2];
+                 gc[2] * opt->background[2] + gp;
     double gam[4];
     orc_sh_basis(d, gam);
     for (int64_t k = 0; k < n; ++k) {
@@ -840,6 +852,10 @@ int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
         double io = rr.io[k];
         double dz = rr.w[k] * gi * io * (1.0 - io);
         for (int a = 0; a < 4; ++a) ADD(&gr[27 + a], dz * xh[a]);
+      }
+      if (opt->want_raydrop) {
+        double dr = rr.dr[k];
+        ADD(&gr[31], rr.w[k] * gp * dr * (1.0 - dr));
       }
     }
     free(gq);

@@ -61,6 +61,7 @@ typedef struct {
   double background[3];
   int32_t want_intensity;
   int32_t brute_force;   /* 1: test every voxel; 0: finest-level DDA candidates */
+  int32_t want_raydrop;  /* evaluate the raydrop field (record slot 31) */
 } orc_opts;
 
 typedef struct {
@@ -75,6 +76,7 @@ typedef struct {
   int32_t* visits;       /* m*visits_cap input voxel indices in order, -1 padded */
   int32_t visits_cap;
   double* max_alpha;     /* n (input order): largest composited alpha per voxel, max-accumulated */
+  double* raydrop;       /* m: sum of w * sigmoid(rho) + T_end (an escaping ray returns nothing) */
 } orc_outputs;
 
 typedef struct {
@@ -109,10 +111,12 @@ int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
                const int64_t* idx, int64_t m, const orc_outputs* out);
 /* grad (n*32, input order) += d/dparams of
  *   sum_r g_rgb[r].rgb[r] + g_depth[r] depth[r] + g_opacity[r] opacity[r]
- *         + g_intensity[r] intensity[r]     (any g_* may be NULL). */
+ *         + g_intensity[r] intensity[r] + g_raydrop[r] raydrop[r]
+ * (any g_* may be NULL). */
 int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
                  const int64_t* idx, int64_t m, const double* g_rgb, const double* g_depth,
-                 const double* g_opacity, const double* g_intensity, double* grad);
+                 const double* g_opacity, const double* g_intensity, const double* g_raydrop,
+                 double* grad);
 int orc_num_threads(void);
 
 /* Sec. III-C densification: the record of child `child` (bits x | y << 1 |
