@@ -81,7 +81,7 @@ typedef struct salf_server salf_server;
  *           C1 = sqrt(3)/(2 sqrt(pi)), w = unit ray direction)
  *   [25] a, [26] b (Eq. 6; SDF mode requires a > 0 and b > 0)
  *   [27:31] W_int: intensity field sigmoid(W_int . [x, 1]), 3 slopes then bias
- *   [31]    unused
+ *   [31]    rho: LiDAR raydrop logit, constant over the voxel (raydrop output)
  * `params` are FP32 (host memory, or device memory if params_on_device);
  * `dtype` selects how the scene stores them (FP32, or BF16 converted by
  * round-to-nearest; all arithmetic is FP32 either way).  level and ijk are
@@ -181,6 +181,10 @@ typedef struct {
  *   ray_dump  R x 8 (debugging aid): the generated ray as (ox, oy, oz, dx, dy,
  *             dz, time, valid) in world coordinates
  *   steps     R (debugging aid): structure leaves the traversal stepped through
+ *   raydrop   R: sum_i T_i alpha_i sigmoid(rho_i) + T_end, the probability that
+ *             the LiDAR return is dropped (a ray that leaves the scene returns
+ *             nothing); Sec. V-C and Table III name raydrop without a form.
+ *             salf_render_rays only (not rasterised, actor or no-alloc renders)
  * on_host = 0: device pointers; on_host = 1: host pointers (the library renders
  * into its own device staging buffers and copies back before returning).
  */
@@ -199,6 +203,7 @@ typedef struct {
   float* max_alpha;  /* n (scene voxels, input order), device, salf_render_rays only:
                         max-accumulated with each voxel's largest composited alpha
                         (Eq. 4) over the rays; the caller zeroes it (pruning, Sec. III-C) */
+  float* raydrop;
 } salf_outputs;
 
 typedef struct {
@@ -273,7 +278,9 @@ salf_status salf_render_rays_host_noalloc(salf_scene* scene, const salf_sensor* 
  * Adjoint of salf_render_rays (gradients of Eq. 1-6 compositing, transmittance
  * recomputed front to back).  `saved` is the R x 8 array the forward call wrote
  * with the same scene, sensor and options.  d_rgb (R x 3), d_depth,
- * d_opacity, d_intensity (R each; NULL = zero) are dL/d(outputs).  d_params
+ * d_opacity, d_intensity, d_raydrop (R each; NULL = zero) are dL/d(outputs);
+ * with d_raydrop, `raydrop` is the forward's raydrop output (R; its composited
+ * part raydrop - T_end enters the suffix sums), else it may be NULL.  d_params
  * (n x 32 FP32, input order, device memory) is ACCUMULATED (+=) with dL/d
  * (record scalars); scalars a field mode does not use receive no gradient.
  * All pointers are device memory.  Asynchronous on `stream`.
@@ -282,6 +289,7 @@ salf_status salf_render_backward(salf_scene* scene, const salf_sensor* sensor,
                                  const salf_render_opts* opts, const float* saved,
                                  const float* d_rgb, const float* d_depth,
                                  const float* d_opacity, const float* d_intensity,
+                                 const float* raydrop, const float* d_raydrop,
                                  float* d_params, void* stream);
 
 /*

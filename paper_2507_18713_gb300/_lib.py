@@ -49,7 +49,8 @@ class Outputs(C.Structure):
     _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("opacity", c_void_p),
                 ("intensity", c_void_p), ("saved", c_void_p), ("valid", c_void_p),
                 ("visit_count", c_void_p), ("visits", c_void_p), ("ray_dump", c_void_p),
-                ("steps", c_void_p), ("on_host", c_int32), ("max_alpha", c_void_p)]
+                ("steps", c_void_p), ("on_host", c_int32), ("max_alpha", c_void_p),
+                ("raydrop", c_void_p)]
 
 
 class SceneInfo(C.Structure):
@@ -112,7 +113,8 @@ SIGNATURES = {
     "salf_render_rays_host_noalloc": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),
                                        C.POINTER(Outputs), c_void_p], c_int32),
     "salf_render_backward": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts), c_void_p,
-                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_void_p], c_int32),
     "salf_scene_check": ([c_void_p], c_int32),
     "salf_serve_create": ([c_void_p, C.c_size_t, c_int32, C.POINTER(c_void_p)], c_int32),
     "salf_serve_submit": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),

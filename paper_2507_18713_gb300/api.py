@@ -197,7 +197,8 @@ class Scene:
         R = n_rays(sensor)
         dev = torch.device("cuda", self.ctx.device)
         res = {} if out is None else dict(out)
-        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,)}
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,),
+                  "raydrop": (R,)}
         for k in outputs:
             if k not in res:
                 res[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
@@ -214,7 +215,7 @@ class Scene:
         if steps and "steps" not in res:
             res["steps"] = torch.empty((R,), dtype=torch.int32, device=dev)
         for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits",
-                  "ray_dump", "steps"):
+                  "ray_dump", "steps", "raydrop"):
             if k in res:
                 setattr(o, k, res[k].data_ptr())
         if max_alpha is not None:
@@ -240,7 +241,8 @@ class Scene:
         R = n_rays(sensor)
         dev = torch.device("cuda", self.ctx.device)
         res = {} if out is None else dict(out)
-        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,)}
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,),
+                  "raydrop": (R,)}
         for k in outputs:
             if k not in res:
                 res[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
@@ -252,7 +254,8 @@ class Scene:
             res.setdefault("visit_count", torch.empty((R,), dtype=torch.int32, device=dev))
             res.setdefault("visits", torch.empty((R, visits_cap), dtype=torch.int32, device=dev))
         o = L.Outputs()
-        for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits"):
+        for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits",
+                  "raydrop"):
             if k in res:
                 setattr(o, k, res[k].data_ptr())
         keep: list = []
@@ -340,7 +343,8 @@ class Scene:
         R = n_rays(sensor)
         dev = torch.device("cuda", self.ctx.device)
         res = {} if out is None else dict(out)
-        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,)}
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,),
+                  "raydrop": (R,)}
         for k in outputs:
             if k not in res:
                 res[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
@@ -352,7 +356,8 @@ class Scene:
             res.setdefault("visit_count", torch.empty((R,), dtype=torch.int32, device=dev))
             res.setdefault("visits", torch.empty((R, visits_cap), dtype=torch.int32, device=dev))
         o = L.Outputs()
-        for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits"):
+        for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "visit_count", "visits",
+                  "raydrop"):
             if k in res:
                 setattr(o, k, res[k].data_ptr())
         arr = (L.Actor * max(1, len(actors)))()
@@ -376,7 +381,8 @@ class Scene:
         """salf_render_rays with host output buffers (on_host = 1): synchronous,
         results land in (pinned, if given) host memory."""
         R = n_rays(sensor)
-        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,)}
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,),
+                  "raydrop": (R,)}
         res = out if out is not None else {k: torch.empty(shapes[k], dtype=torch.float32)
                                            for k in outputs}
         o = L.Outputs()
@@ -396,7 +402,8 @@ class Scene:
         """salf_render_rays_host_noalloc: like render_host, but the library
         stages the outputs in its fixed device array instead of allocating."""
         R = n_rays(sensor)
-        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,), "valid": (R,)}
+        shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,), "valid": (R,),
+                  "raydrop": (R,)}
         res = out if out is not None else {
             k: torch.empty(shapes[k], dtype=torch.uint8 if k == "valid" else torch.float32)
             for k in outputs}
@@ -413,9 +420,10 @@ class Scene:
 
     def backward(self, sensor: dict, saved, d_rgb=None, d_depth=None, d_opacity=None,
                  d_intensity=None, d_params=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
-                 want_intensity=False, stream=None):
+                 want_intensity=False, stream=None, raydrop=None, d_raydrop=None):
         """salf_render_backward: returns d_params (n, 32) float32 (accumulated
-        into the given tensor if any)."""
+        into the given tensor if any).  With d_raydrop, `raydrop` is the
+        forward's raydrop output."""
         dev = torch.device("cuda", self.ctx.device)
         if d_params is None:
             d_params = torch.zeros((self.n, 32), dtype=torch.float32, device=dev)
@@ -423,12 +431,14 @@ class Scene:
         def ptr(t):
             return None if t is None else t.contiguous().data_ptr()
 
-        keep = [t.contiguous() for t in (d_rgb, d_depth, d_opacity, d_intensity) if t is not None]
+        keep = [t.contiguous() for t in (d_rgb, d_depth, d_opacity, d_intensity, raydrop,
+                                         d_raydrop) if t is not None]
         s = sensor_struct(sensor, keep)
         op = opts_struct(t_min, background, want_intensity, 0)
         L.check(L.load().salf_render_backward(
             self._h, C.byref(s), C.byref(op), saved.data_ptr(), ptr(d_rgb), ptr(d_depth),
-            ptr(d_opacity), ptr(d_intensity), d_params.data_ptr(), _stream_ptr(stream)),
+            ptr(d_opacity), ptr(d_intensity), ptr(raydrop), ptr(d_raydrop), d_params.data_ptr(),
+            _stream_ptr(stream)),
             "salf_render_backward")
         return d_params
 

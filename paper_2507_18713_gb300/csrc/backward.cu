@@ -10,7 +10,9 @@
 // then chains through Eq. 1 (d sigma / d W = sigma [x, 1]) or Eq. 5-6
 // (d sigma / d s = a e^{-|s|/b} / (2b), d sigma / d a = sigma / a,
 //  d sigma / d b = -a s e^{-|s|/b} / (2 b^2)) and Eq. 2 (d c / d z = c (1 - c),
-// d z / d W_c = x, d z / d W_sh = gamma).  Gradients go to the caller's
+// d z / d W_c = x, d z / d W_sh = gamma).  The raydrop output adds
+// q_k = sigmoid(rho_k) and a background of 1 (T_end), and d/d rho_k =
+// w_k s (1 - s).  Gradients go to the caller's
 // input-order FP32 buffer with 16-byte vector atomics; lanes of a warp that
 // hit the same voxel in the same round stage their rows in shared memory and
 // share the summing: each adds some of the 16-byte chunks over the group, so
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
   r.valid = false;
   r.d[0] = r.d[1] = r.d[2] = 0.f;
   float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  float gQ = 0.f, Tend = 1.f;
+  float gQ = 0.f, Tend = 1.f, gp = 0.f;
   int nv = 0;
   if (in_img) {
     gen_ray(Q, S, u, v, ray, r);
@@ -65,6 +67,10 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
     if (Q.g_int && Q.want_int) g[5] = __ldg(Q.g_int + ray);
     gQ = g[0] * s0.x + g[1] * s0.y + g[2] * s0.z + g[3] * s0.w + g[4] * s1.x + g[5] * s1.y;
     Tend = s1.z;
+    if (Q.g_raydrop) {  // composited part of the raydrop output: raydrop - T_end
+      gp = __ldg(Q.g_raydrop + ray);
+      gQ = fmaf(gp, __ldg(Q.b_raydrop + ray) - Tend, gQ);
+    }
     nv = (int)s1.w;
     if (!r.valid) nv = 0;
     if (nv == 0) w.alive = false;
@@ -72,7 +78,8 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
   float gam[4];
   sh_basis(r.d, gam);
   const bool want_int = Q.want_int != 0;
-  const float gbg = g[0] * Q.bg[0] + g[1] * Q.bg[1] + g[2] * Q.bg[2];
+  const bool want_drop = Q.g_raydrop != nullptr;
+  const float gbg = g[0] * Q.bg[0] + g[1] * Q.bg[1] + g[2] * Q.bg[2] + gp;
   float T = 1.f, Pk = 0.f;
   int k = 0;
   __shared__ float s_rows[SALF_BWD_WARPS][32][33];  // padded: conflict-free columns
@@ -90,12 +97,13 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
       float x[3];
       local_coords(w, h, tm, x);
       Field f;
-      field_eval<DT, MODE>(S, h.vox, want_int, x, gam, f);
+      field_eval<DT, MODE>(S, h.vox, want_int, x, gam, f, want_drop);
       const float sig = f.sig, lin = f.lin, io = f.io;
       const float* c = f.c;
       const float e = __expf(-sig * dl);
       const float wgt = T * (1.f - e);
-      const float gq = g[0] * c[0] + g[1] * c[1] + g[2] * c[2] + g[3] * tm + g[4] + g[5] * io;
+      const float gq =
+          g[0] * c[0] + g[1] * c[1] + g[2] * c[2] + g[3] * tm + g[4] + g[5] * io + gp * f.dr;
       Pk = fmaf(wgt, gq, Pk);
       const float Tn = T * e;
       const float dtau = Tn * gq - (gQ - Pk) - Tend * gbg;
@@ -130,9 +138,10 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
 #pragma unroll
         for (int q = 0; q < 4; ++q) gr[27 + q] = dz * xh[q];
       }
+      if (want_drop) gr[31] = wgt * gp * f.dr * (1.f - f.dr);
       const int key = __ldg(&S.order[h.vox]);
       const unsigned peers = __match_any_sync(hit_lanes, key);
-      const int nq = want_int ? 8 : 7;
+      const int nq = (want_int || want_drop) ? 8 : 7;
       float4* dst = reinterpret_cast<float4*>(Q.d_params) + (size_t)key * 8;
       if (peers == (1u << lane)) {
 #pragma unroll

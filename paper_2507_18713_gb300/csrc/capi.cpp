@@ -414,7 +414,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
   }
   const salf_render_opts o = opts ? *opts : default_opts();
   if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
-      !(o.visits_cap > 0 && out->visits) && !out->ray_dump && !out->steps) {
+      !(o.visits_cap > 0 && out->visits) && !out->ray_dump && !out->steps && !out->raydrop) {
     g_err = "salf_render_rays: no output requested";
     return SALF_ERR_INVALID;
   }
@@ -457,6 +457,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
     r.ray_dump = out->ray_dump;
     r.steps_out = out->steps;
     r.max_alpha = reinterpret_cast<unsigned*>(out->max_alpha);
+    r.raydrop = out->raydrop;
     if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
     return SALF_OK;
   }
@@ -465,12 +466,12 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
   std::lock_guard<std::mutex> lk(sc->staging_mu);
   const size_t vcap = (size_t)std::max(0, o.visits_cap);
   const size_t rays_bytes = sen->kind == SALF_RAYS_EXPLICIT ? R * 32 : 0;
-  size_t off[9], total = 0;
-  const size_t sizes[9] = {out->rgb ? R * 12 : 0, out->depth ? R * 4 : 0, out->opacity ? R * 4 : 0,
-                           out->intensity ? R * 4 : 0, out->saved ? R * 32 : 0,
-                           out->valid ? R : 0, vcap ? R * 4 : 0, vcap ? R * vcap * 4 : 0,
-                           rays_bytes};
-  for (int i = 0; i < 9; ++i) {
+  size_t off[10], total = 0;
+  const size_t sizes[10] = {out->rgb ? R * 12 : 0, out->depth ? R * 4 : 0, out->opacity ? R * 4 : 0,
+                            out->intensity ? R * 4 : 0, out->saved ? R * 32 : 0,
+                            out->valid ? R : 0, vcap ? R * 4 : 0, vcap ? R * vcap * 4 : 0,
+                            rays_bytes, out->raydrop ? R * 4 : 0};
+  for (int i = 0; i < 10; ++i) {
     off[i] = total;
     total += (sizes[i] + 255) & ~(size_t)255;
   }
@@ -484,6 +485,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
   r.valid = out->valid ? reinterpret_cast<unsigned char*>(base + off[5]) : nullptr;
   r.vcount = vcap ? reinterpret_cast<int*>(base + off[6]) : nullptr;
   r.visits = vcap ? reinterpret_cast<int*>(base + off[7]) : nullptr;
+  r.raydrop = out->raydrop ? reinterpret_cast<float*>(base + off[9]) : nullptr;
   if (rays_bytes) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, sen->rays) == cudaSuccess && at.type == cudaMemoryTypeDevice) {
@@ -501,10 +503,11 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
     void* dst;
     const void* src;
     size_t n;
-  } cps[8] = {{out->rgb, r.rgb, sizes[0]},        {out->depth, r.depth, sizes[1]},
+  } cps[9] = {{out->rgb, r.rgb, sizes[0]},        {out->depth, r.depth, sizes[1]},
               {out->opacity, r.opacity, sizes[2]}, {out->intensity, r.intensity, sizes[3]},
               {out->saved, r.saved, sizes[4]},     {out->valid, r.valid, sizes[5]},
-              {out->visit_count, r.vcount, sizes[6]}, {out->visits, r.visits, sizes[7]}};
+              {out->visit_count, r.vcount, sizes[6]}, {out->visits, r.visits, sizes[7]},
+              {out->raydrop, r.raydrop, sizes[9]}};
   for (const Cp& c : cps) {
     if (!c.n || !c.dst) continue;
     if ((e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
@@ -534,8 +537,8 @@ extern "C" salf_status salf_render_raster(salf_scene* sc, const salf_sensor* sen
     return SALF_ERR_INVALID;
   }
   const salf_render_opts o = opts ? *opts : default_opts();
-  if (out->on_host || out->ray_dump || out->steps) {
-    g_err = "salf_render_raster: device outputs only (no ray_dump or steps)";
+  if (out->on_host || out->ray_dump || out->steps || out->raydrop) {
+    g_err = "salf_render_raster: device outputs only (no ray_dump, steps or raydrop)";
     return SALF_ERR_INVALID;
   }
   if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
@@ -634,8 +637,8 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
     return SALF_ERR_INVALID;
   }
   const salf_render_opts o = opts ? *opts : default_opts();
-  if (out->on_host || out->ray_dump || out->steps) {
-    g_err = "salf_render_rays_actors: device outputs only (no ray_dump or steps)";
+  if (out->on_host || out->ray_dump || out->steps || out->raydrop) {
+    g_err = "salf_render_rays_actors: device outputs only (no ray_dump, steps or raydrop)";
     return SALF_ERR_INVALID;
   }
   if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
@@ -830,9 +833,14 @@ extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* s
                                             const salf_render_opts* opts, const float* saved,
                                             const float* d_rgb, const float* d_depth,
                                             const float* d_opacity, const float* d_intensity,
+                                            const float* raydrop, const float* d_raydrop,
                                             float* d_params, void* stream) {
   if (!sc || !sen || !saved || !d_params) {
     g_err = "salf_render_backward: null argument";
+    return SALF_ERR_INVALID;
+  }
+  if (d_raydrop && !raydrop) {
+    g_err = "salf_render_backward: d_raydrop needs the forward's raydrop output";
     return SALF_ERR_INVALID;
   }
   if (misaligned(saved, 16) || misaligned(d_params, 16)) {
@@ -856,6 +864,8 @@ extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* s
   r.g_depth = d_depth;
   r.g_opacity = d_opacity;
   r.g_int = d_intensity;
+  r.b_raydrop = d_raydrop ? raydrop : nullptr;
+  r.g_raydrop = d_raydrop;
   r.d_params = d_params;
   P.total_tiles = r.n_tiles;
   P.step_budget = salf_step_budget();

@@ -62,9 +62,9 @@ extern "C" salf_status salf_render_rays_host_noalloc(salf_scene* sc, const salf_
     salf_set_error("salf_render_rays_host_noalloc: null argument");
     return SALF_ERR_INVALID;
   }
-  if (out->visits || out->visit_count || out->ray_dump || out->steps ||
+  if (out->visits || out->visit_count || out->ray_dump || out->steps || out->raydrop ||
       (opts && opts->visits_cap > 0)) {
-    salf_set_error("salf_render_rays_host_noalloc: debug outputs are not supported");
+    salf_set_error("salf_render_rays_host_noalloc: debug and raydrop outputs are not supported");
     return SALF_ERR_INVALID;
   }
   if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid) {

@@ -72,7 +72,9 @@ __device__ __forceinline__ void span_products(float T, int k, int K, float* inc,
   *ex = k == 0 ? 1.f : e;
 }
 
-template <int DT, int MODE, bool DUMP, int WPB, int MINB, bool SEG>
+// RD: the variant can write the raydrop output (instantiated only for
+// batches that ask for it, so the other variants keep their code).
+template <int DT, int MODE, bool DUMP, int WPB, int MINB, bool SEG, bool RD>
 __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constant__ LaunchParams P) {
   const int warp = blockIdx.x * WPB + (threadIdx.x >> 5);
   if (warp >= P.total_tiles) return;
@@ -124,8 +126,9 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   float gam[4];
   sh_basis(r.d, gam);
   const bool want_int = Q.want_int != 0;
+  const bool want_drop = RD && Q.raydrop != nullptr;
   const float tmin = Q.t_min;
-  Accum A{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+  Accum A{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0.f};
   float T_prev = 1.f;  // SEG: this span's T before its last composited hit
   bool keep = true;    // SEG: the whole ray reaches this lane's span
 
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
         const GlobalRec src{reinterpret_cast<const float4*>(S.params) +
                             (size_t)h.vox * RecordLayout<DT>::kChunks};
         if (SEG) T_prev = A.T;
-        const float e = composite_hit<DT, MODE>(w, h, src, want_int, gam, A);
+        const float e = composite_hit<DT, MODE>(w, h, src, want_int, gam, A, want_drop);
         if (DUMP) {
           if (A.nvis < Q.vcap) Q.visits[(size_t)ray * Q.vcap + A.nvis] = __ldg(&S.order[h.vox]);
           if (Q.max_alpha)  // alpha >= 0: FP32 bit patterns order like the values
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
     // else it composited past the stop: walk it again from Tf
     const bool redo = keep && ends && Tf < 1.f && !(Tf * T_prev >= tmin);
     if (redo) {
-      A = Accum{Tf, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+      A = Accum{Tf, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0.f};
       walk_seek(S, w, cut_lo);
       w.alive = true;
     } else if (keep) {
@@ -189,26 +192,28 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
       A.C2 *= Tf;
       A.Dp *= Tf;
       A.Ip *= Tf;
+      if (want_drop) A.Rp *= Tf;
       A.T *= Tf;
     }
     if (!__any_sync(0xffffffffu, redo)) break;
   }
   if (SEG && ks > 0) {
     // sum the kept spans; the ray's final T is the smallest kept one (T only falls)
-    if (!keep) A = Accum{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    if (!keep) A = Accum{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0.f};
     for (int off = K >> 1; off > 0; off >>= 1) {
       A.C0 += __shfl_xor_sync(0xffffffffu, A.C0, off, K);
       A.C1 += __shfl_xor_sync(0xffffffffu, A.C1, off, K);
       A.C2 += __shfl_xor_sync(0xffffffffu, A.C2, off, K);
       A.Dp += __shfl_xor_sync(0xffffffffu, A.Dp, off, K);
       A.Ip += __shfl_xor_sync(0xffffffffu, A.Ip, off, K);
+      if (want_drop) A.Rp += __shfl_xor_sync(0xffffffffu, A.Rp, off, K);
       A.T = fminf(A.T, __shfl_xor_sync(0xffffffffu, A.T, off, K));
       A.nvis += __shfl_xor_sync(0xffffffffu, A.nvis, off, K);
     }
     if (kseg != 0) return;
   }
   if (!in_img) return;
-  write_outputs(Q, ray, r.valid, A);
+  write_outputs(Q, ray, r.valid, A, want_drop);
   if (DUMP) {
     if (Q.steps_out) Q.steps_out[ray] = w.steps;
     if (Q.vcap > 0) {
@@ -218,44 +223,52 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   }
 }
 
-template <int DT, int MODE, bool DUMP, int WPB, int MINB, bool SEG>
+template <int DT, int MODE, bool DUMP, int WPB, int MINB, bool SEG, bool RD>
 static void launch_one(const LaunchParams& P, cudaStream_t st) {
   const int blocks = (P.total_tiles + WPB - 1) / WPB;
-  if (blocks > 0) k_forward<DT, MODE, DUMP, WPB, MINB, SEG><<<blocks, 32 * WPB, 0, st>>>(P);
+  if (blocks > 0) k_forward<DT, MODE, DUMP, WPB, MINB, SEG, RD><<<blocks, 32 * WPB, 0, st>>>(P);
 }
 
 template <int DT, int MODE>
-static cudaError_t launch_fm(const LaunchParams& P, bool dump, bool coherent, bool seg,
+static cudaError_t launch_fm(const LaunchParams& P, bool dump, bool coherent, bool seg, bool rd,
                              cudaStream_t st) {
+  constexpr int WD = SALF_FWD_WPB_DIVERGENT, BD = SALF_FWD_BLOCKS_DIVERGENT;
+  constexpr int WS = SALF_FWD_WPB_SEG, BS = SALF_FWD_BLOCKS_SEG;
   if (dump)
-    launch_one<DT, MODE, true, SALF_FWD_WPB_DIVERGENT, SALF_FWD_BLOCKS_DIVERGENT, false>(P, st);
+    launch_one<DT, MODE, true, WD, BD, false, true>(P, st);
+  else if (seg && rd)
+    launch_one<DT, MODE, false, WS, BS, true, true>(P, st);
   else if (seg)
-    launch_one<DT, MODE, false, SALF_FWD_WPB_SEG, SALF_FWD_BLOCKS_SEG, true>(P, st);
+    launch_one<DT, MODE, false, WS, BS, true, false>(P, st);
+  else if (rd)
+    launch_one<DT, MODE, false, WD, BD, false, true>(P, st);
   else if (coherent)
-    launch_one<DT, MODE, false, SALF_FWD_WPB_COHERENT, SALF_FWD_BLOCKS_COHERENT, false>(P, st);
+    launch_one<DT, MODE, false, SALF_FWD_WPB_COHERENT, SALF_FWD_BLOCKS_COHERENT, false, false>(P,
+                                                                                              st);
   else
-    launch_one<DT, MODE, false, SALF_FWD_WPB_DIVERGENT, SALF_FWD_BLOCKS_DIVERGENT, false>(P, st);
+    launch_one<DT, MODE, false, WD, BD, false, false>(P, st);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_variant(const LaunchParams& P, cudaStream_t st) {
-  bool dump = false, coherent = true, seg = false;
+  bool dump = false, coherent = true, seg = false, rd = false;
   for (int i = 0; i < P.n_req; ++i) {
     const ReqDev& q = P.req[i];
     dump = dump || q.vcap > 0 || q.ray_dump || q.steps_out || q.max_alpha;
     coherent = coherent && ((SALF_FWD_COHERENT_KINDS >> q.kind) & 1);
     seg = seg || q.seg_shift > 0;
+    rd = rd || q.raydrop;
   }
   // the debug variant walks whole rays: its requests must be tiled for that
   if (dump && seg) return cudaErrorInvalidValue;
   const int dt = P.S.dtype, md = P.S.mode;
   if (dt == SALF_F32 && md == SALF_FIELD_EXP)
-    return launch_fm<SALF_F32, SALF_FIELD_EXP>(P, dump, coherent, seg, st);
+    return launch_fm<SALF_F32, SALF_FIELD_EXP>(P, dump, coherent, seg, rd, st);
   if (dt == SALF_F32 && md == SALF_FIELD_SDF)
-    return launch_fm<SALF_F32, SALF_FIELD_SDF>(P, dump, coherent, seg, st);
+    return launch_fm<SALF_F32, SALF_FIELD_SDF>(P, dump, coherent, seg, rd, st);
   if (dt == SALF_BF16 && md == SALF_FIELD_EXP)
-    return launch_fm<SALF_BF16, SALF_FIELD_EXP>(P, dump, coherent, seg, st);
-  return launch_fm<SALF_BF16, SALF_FIELD_SDF>(P, dump, coherent, seg, st);
+    return launch_fm<SALF_BF16, SALF_FIELD_EXP>(P, dump, coherent, seg, rd, st);
+  return launch_fm<SALF_BF16, SALF_FIELD_SDF>(P, dump, coherent, seg, rd, st);
 }
 
 // A batch that mixes span-parallel requests with whole-ray ones runs as two

@@ -121,6 +121,7 @@ struct ReqDev {
   float* ray_dump;
   int* steps_out;
   unsigned* max_alpha;  // per voxel (input order): largest alpha, as FP32 bits (alpha >= 0)
+  float* raydrop;       // sum T_i alpha_i sigmoid(rho_i) + T_end
   float t_min;
   float bg[3];
   int want_int;
@@ -143,6 +144,8 @@ struct ReqDev {
   const float* g_depth;
   const float* g_opacity;
   const float* g_int;
+  const float* b_raydrop;  // the forward's raydrop output
+  const float* g_raydrop;
   float* d_params;
 };
 

@@ -571,6 +571,7 @@ __device__ __forceinline__ void tile_origin(const ReqDev& Q, int tile, int* u0, 
 // intensity, and the SDF parameters a, b.
 struct Field {
   float sig, lin, c[3], io, a, b;
+  float dr;  // sigmoid of the raydrop logit (record slot 31), when asked for
 };
 
 __device__ __forceinline__ float sdf_density(float s, float a, float b) {
@@ -585,7 +586,8 @@ __device__ __forceinline__ float sdf_density(float s, float a, float b) {
 // r, g, b), W_sh 13-24 (rows r, g, b), a 25, b 26, W_int 27-30.
 template <int DT, int MODE, class Src>
 __device__ __forceinline__ void field_eval_src(const Src& p, bool want_int, const float x[3],
-                                               const float gam[4], Field& f) {
+                                               const float gam[4], Field& f,
+                                               bool want_drop = false) {
   if constexpr (DT == SALF_F32) {
     const float4 q0 = p.chunk(0), q1 = p.chunk(1), q2 = p.chunk(2), q3 = p.chunk(3);
     f.lin = fmaf(q0.x, x[0], fmaf(q0.y, x[1], fmaf(q0.z, x[2], q0.w)));
@@ -613,9 +615,12 @@ __device__ __forceinline__ void field_eval_src(const Src& p, bool want_int, cons
     f.c[1] = sigmoidf_fast(zg);
     f.c[2] = sigmoidf_fast(zb);
     f.io = 0.f;
-    if (want_int) {
+    f.dr = 0.f;
+    if (want_int || want_drop) {
       const float4 q7 = p.chunk(7);
-      f.io = sigmoidf_fast(fmaf(q6.w, x[0], fmaf(q7.x, x[1], fmaf(q7.y, x[2], q7.z))));
+      if (want_int)
+        f.io = sigmoidf_fast(fmaf(q6.w, x[0], fmaf(q7.x, x[1], fmaf(q7.y, x[2], q7.z))));
+      if (want_drop) f.dr = sigmoidf_fast(q7.w);
     }
   } else {
     Record<DT> rec;
@@ -623,6 +628,7 @@ __device__ __forceinline__ void field_eval_src(const Src& p, bool want_int, cons
     f.sig = density<MODE>(rec.v, x, &f.lin);
     colour(rec.v, x, gam, f.c);
     f.io = want_int ? intensity_field(rec.v, x) : 0.f;
+    f.dr = want_drop ? sigmoidf_fast(rec.v[31]) : 0.f;
     f.a = rec.v[25];
     f.b = rec.v[26];
   }
@@ -636,16 +642,18 @@ struct RecordLayout {
 
 template <int DT, int MODE>
 __device__ __forceinline__ void field_eval(const DevScene& S, int vox, bool want_int,
-                                           const float x[3], const float gam[4], Field& f) {
+                                           const float x[3], const float gam[4], Field& f,
+                                           bool want_drop = false) {
   const GlobalRec src{reinterpret_cast<const float4*>(S.params) +
                       (size_t)vox * RecordLayout<DT>::kChunks};
-  field_eval_src<DT, MODE>(src, want_int, x, gam, f);
+  field_eval_src<DT, MODE>(src, want_int, x, gam, f, want_drop);
 }
 
 // Front-to-back accumulators of one ray (Eq. 3-4).
 struct Accum {
   float T, C0, C1, C2, Dp, Ip;
   int nvis;
+  float Rp;  // sum of T_i alpha_i sigmoid(rho_i) (raydrop, when asked for)
 };
 
 // Composite one hit voxel with its field at the segment midpoint: alpha =
@@ -654,13 +662,14 @@ struct Accum {
 // Returns 1 - alpha.
 template <int DT, int MODE, class Src>
 __device__ __forceinline__ float composite_hit(const Walk& w, const Hit& h, const Src& src,
-                                              bool want_int, const float gam[4], Accum& A) {
+                                              bool want_int, const float gam[4], Accum& A,
+                                              bool want_drop = false) {
   const float tm = 0.5f * (h.tin + h.tout);
   const float dl = h.tout - h.tin;
   float x[3];
   local_coords(w, h, tm, x);
   Field f;
-  field_eval_src<DT, MODE>(src, want_int, x, gam, f);
+  field_eval_src<DT, MODE>(src, want_int, x, gam, f, want_drop);
   const float e = __expf(-f.sig * dl);  // 1 - alpha (Eq. 4)
   const float wgt = A.T * (1.f - e);    // T_i alpha_i (Eq. 3)
   A.C0 = fmaf(wgt, f.c[0], A.C0);
@@ -668,13 +677,17 @@ __device__ __forceinline__ float composite_hit(const Walk& w, const Hit& h, cons
   A.C2 = fmaf(wgt, f.c[2], A.C2);
   A.Dp = fmaf(wgt, tm, A.Dp);
   A.Ip = fmaf(wgt, f.io, A.Ip);
+  if (want_drop) A.Rp = fmaf(wgt, f.dr, A.Rp);
   A.T *= e;
   return e;
 }
 
 // Per-ray outputs of a request (colour premultiplied, background added with
 // the final transmittance; opacity 1 - T_end, which the weights sum to).
-__device__ __forceinline__ void write_outputs(const ReqDev& Q, int ray, bool valid, const Accum& A) {
+__device__ __forceinline__ void write_outputs(const ReqDev& Q, int ray, bool valid, const Accum& A,
+                                              bool want_drop = false) {
+  // raydrop: an escaping ray (T_end) returns nothing
+  if (want_drop) Q.raydrop[ray] = valid ? A.Rp + A.T : 0.f;
   if (Q.rgb) {
     float* o = Q.rgb + 3 * (size_t)ray;
     o[0] = valid ? fmaf(A.T, Q.bg[0], A.C0) : 0.f;

@@ -34,7 +34,7 @@ def test_struct_layouts_match_header():
     """ctypes mirrors use the C layout; spot-check sizes against hand counts."""
     from paper_2507_18713_gb300 import _lib as L
     assert ctypes.sizeof(L.RenderOpts) == 4 + 12 + 4 + 4 + 4
-    assert ctypes.sizeof(L.Outputs) == 10 * 8 + 8 + 8
+    assert ctypes.sizeof(L.Outputs) == 10 * 8 + 8 + 8 + 8
     # kind,width,height + 7 floats = 40 -> pad to 8 -> 2*96 poses -> t0,t1 -> int + 2 floats -> ptr
     assert ctypes.sizeof(L.Sensor) == 40 + 192 + 16 + 12 + 4 + 8
     assert ctypes.sizeof(L.RasterStats) == 8 + 8 + 4 + 4 + 4 + 4
