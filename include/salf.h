@@ -185,8 +185,11 @@ typedef struct {
  *             the LiDAR return is dropped (a ray that leaves the scene returns
  *             nothing); Sec. V-C and Table III name raydrop without a form.
  *             salf_render_rays only (not rasterised, actor or no-alloc renders)
- * on_host = 0: device pointers; on_host = 1: host pointers (the library renders
- * into its own device staging buffers and copies back before returning).
+ * on_host = 0: device pointers; on_host = 1: host pointers, and the call
+ * returns when they hold the results.  Page-locked buffers the device can
+ * address (cudaHostAlloc / cudaHostRegister under unified addressing; saved
+ * 16-byte aligned) are written by the kernel in place; otherwise the library
+ * renders into its own device staging buffers and copies back.
  */
 typedef struct {
   float* rgb;

@@ -462,10 +462,65 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
     return SALF_OK;
   }
 
-  // Host outputs: render into staging, copy back, wait.
-  std::lock_guard<std::mutex> lk(sc->staging_mu);
   const size_t vcap = (size_t)std::max(0, o.visits_cap);
   const size_t rays_bytes = sen->kind == SALF_RAYS_EXPLICIT ? R * 32 : 0;
+  // Host outputs in page-locked memory the device can address (any
+  // cudaHostAlloc / cudaHostRegister buffer under unified addressing): the
+  // kernel writes them in place (over NVLink-C2C on Grace systems): no staging
+  // buffer and no copy step.  Pageable buffers take the staging path below.
+  {
+    const void* hp[9] = {out->rgb,   out->depth,
+                         out->opacity, out->intensity,
+                         out->saved, out->valid,
+                         vcap ? out->visit_count : nullptr, vcap ? out->visits : nullptr,
+                         out->raydrop};
+    void* dp[9] = {};
+    bool direct = !misaligned(out->saved, 16);
+    for (int i = 0; i < 9 && direct; ++i) {
+      if (!hp[i]) continue;
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, hp[i]) != cudaSuccess) {
+        cudaGetLastError();
+        direct = false;
+      } else if (at.type != cudaMemoryTypeHost || !at.devicePointer) {
+        direct = false;
+      } else {
+        dp[i] = at.devicePointer;
+      }
+    }
+    if (direct && rays_bytes) {
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, sen->rays) != cudaSuccess) {
+        cudaGetLastError();
+        direct = false;
+      } else if (at.type == cudaMemoryTypeDevice) {
+        r.rays = sen->rays;
+      } else if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        r.rays = static_cast<const float*>(at.devicePointer);
+      } else {
+        direct = false;
+      }
+    }
+    if (direct) {
+      r.rgb = static_cast<float*>(dp[0]);
+      r.depth = static_cast<float*>(dp[1]);
+      r.opacity = static_cast<float*>(dp[2]);
+      r.intensity = static_cast<float*>(dp[3]);
+      r.saved = static_cast<float*>(dp[4]);
+      r.valid = static_cast<unsigned char*>(dp[5]);
+      r.vcount = static_cast<int*>(dp[6]);
+      r.visits = static_cast<int*>(dp[7]);
+      r.raydrop = static_cast<float*>(dp[8]);
+      if ((e = salf_launch_forward(P, cs)) != cudaSuccess)
+        return salf_cuda_fail(e, "forward launch");
+      if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return salf_cuda_fail(e, "render");
+      return SALF_OK;
+    }
+    r.rays = sen->rays;
+  }
+
+  // Host outputs: render into staging, copy back, wait.
+  std::lock_guard<std::mutex> lk(sc->staging_mu);
   size_t off[10], total = 0;
   const size_t sizes[10] = {out->rgb ? R * 12 : 0, out->depth ? R * 4 : 0, out->opacity ? R * 4 : 0,
                             out->intensity ? R * 4 : 0, out->saved ? R * 32 : 0,

@@ -1,5 +1,6 @@
 """GPU (sm_103a kernels, called through the C ABI) vs the FP64 oracle."""
 
+import ctypes as C
 import math
 
 import numpy as np
@@ -235,6 +236,53 @@ def test_host_outputs_match_device_outputs(salf):
                          outputs=("rgb", "depth", "opacity", "intensity"))
     for k in ("rgb", "depth", "opacity", "intensity"):
         assert np.array_equal(dev[k], host[k].numpy()), k
+
+
+def test_pinned_host_outputs_are_written_in_place(salf):
+    """Page-locked host outputs are written by the kernel directly; pageable
+    ones go through staging; both equal the device outputs bit for bit."""
+    from paper_2507_18713_gb300.api import opts_struct, sensor_struct
+    sc = synth.random_multilevel_scene(seed=5, max_level=2, dims=(6, 5, 4), p_occ=0.7)
+    sc.params[:, 31] = np.random.default_rng(2).normal(size=sc.n)
+    g = salf.Scene(sc)
+    cam = synth.pinhole(641, 479, 75.0, synth.camera_pose_looking((-2.2, 0.6, 1.1), 0.15))
+    lid = synth.lidar(32, 256, synth.lidar_pose((0.35, 0.55, 1.05), 0.2),
+                      synth.lidar_pose((0.95, 0.7, 1.05), 0.45), t0=0.0, t1=0.1)
+    for sen, outs, vcap in ((cam, ("rgb", "depth", "opacity"), 0),
+                            (lid, ("depth", "opacity", "intensity", "raydrop"), 0),
+                            (cam, ("opacity",), 16)):
+        dev = g.render(sen, want_intensity=True, outputs=outs, saved=True, visits_cap=vcap)
+        torch.cuda.synchronize()
+        ref = {k: v.cpu() for k, v in dev.items() if not k.startswith("_")}
+        for pinned in (True, False):
+            host = {k: (torch.empty_like(v).pin_memory() if pinned else torch.empty_like(v))
+                    for k, v in ref.items()}
+            o = salf._lib.Outputs()
+            for k, v in host.items():
+                setattr(o, k, v.data_ptr())
+            o.on_host = 1
+            keep: list = []
+            s = sensor_struct(sen, keep)
+            op = opts_struct(1e-4, (0.0, 0.0, 0.0), True, vcap)
+            st = salf._lib.load().salf_render_rays(g._h, C.byref(s), C.byref(op), C.byref(o), None)
+            assert st == 0
+            for k in ref:
+                assert torch.equal(ref[k], host[k]), (sen["kind"], k, pinned)
+    # explicit rays in page-locked memory, read by the kernel in place
+    rng = np.random.default_rng(4)
+    r = np.concatenate([rng.uniform(-1, 2, (777, 3)), rng.normal(size=(777, 3)),
+                        np.zeros((777, 2))], axis=1).astype(np.float32)
+    r[:, 3:6] /= np.linalg.norm(r[:, 3:6], axis=1, keepdims=True)
+    pr = torch.from_numpy(r).pin_memory()
+    sen_h = synth.explicit_rays(r)
+    sen_h["rays"] = pr
+    dev = g.render(synth.explicit_rays(r), outputs=("rgb", "depth"))
+    host = g.render_host(sen_h, outputs=("rgb", "depth"),
+                         out={"rgb": torch.empty((777, 3)).pin_memory(),
+                              "depth": torch.empty(777).pin_memory()})
+    torch.cuda.synchronize()
+    assert torch.equal(dev["rgb"].cpu(), host["rgb"]) and torch.equal(dev["depth"].cpu(), host["depth"])
+    g.check()
 
 
 def test_update_params_matches_rebuild(salf):
