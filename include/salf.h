@@ -261,7 +261,9 @@ salf_status salf_render_rays(salf_scene* scene, const salf_sensor* sensor,
  * device memory is reserved up front by their own pooling allocator, and
  * plug-ins whose host forbids them to allocate.  (salf_render_rays with
  * on_host = 1 grows a staging buffer with cudaMalloc instead.)
- * The outputs are staged in a fixed 48 MiB array compiled into the library
+ * Page-locked host buffers the device can address (cudaHostAlloc /
+ * cudaHostRegister; saved 16-byte aligned) are written by the kernel in place.
+ * Other buffers are staged in a fixed 48 MiB array compiled into the library
  * (every device that loads the library holds it until the process exits);
  * requests whose outputs need more staging than that are rejected with
  * SALF_ERR_INVALID.  `out` holds host pointers (on_host is ignored); the

@@ -96,6 +96,40 @@ extern "C" salf_status salf_render_rays_host_noalloc(salf_scene* sc, const salf_
       return SALF_ERR_INVALID;
     }
   }
+  P.total_tiles = r.n_tiles;
+  P.step_budget = salf_step_budget();
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  // page-locked, device-addressable host outputs: the kernel writes them in
+  // place (no staging, no copy step)
+  {
+    void* hp[6] = {out->rgb, out->depth, out->opacity, out->intensity, out->saved, out->valid};
+    void* dp[6] = {};
+    bool direct = (reinterpret_cast<uintptr_t>(out->saved) & 15u) == 0;
+    for (int i = 0; i < 6 && direct; ++i) {
+      if (!hp[i]) continue;
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, hp[i]) != cudaSuccess) {
+        cudaGetLastError();
+        direct = false;
+      } else if (at.type != cudaMemoryTypeHost || !at.devicePointer) {
+        direct = false;
+      } else {
+        dp[i] = at.devicePointer;
+      }
+    }
+    if (direct) {
+      r.rgb = static_cast<float*>(dp[0]);
+      r.depth = static_cast<float*>(dp[1]);
+      r.opacity = static_cast<float*>(dp[2]);
+      r.intensity = static_cast<float*>(dp[3]);
+      r.saved = static_cast<float*>(dp[4]);
+      r.valid = static_cast<unsigned char*>(dp[5]);
+      if ((e = salf_launch_forward(P, cs)) != cudaSuccess)
+        return salf_cuda_fail(e, "forward launch");
+      if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return salf_cuda_fail(e, "render");
+      return SALF_OK;
+    }
+  }
   const size_t R = (size_t)salf_request_rays(sen);
   const size_t sizes[6] = {out->rgb ? R * 12 : 0,       out->depth ? R * 4 : 0,
                            out->opacity ? R * 4 : 0,    out->intensity ? R * 4 : 0,
@@ -119,9 +153,6 @@ extern "C" salf_status salf_render_rays_host_noalloc(salf_scene* sc, const salf_
   r.intensity = out->intensity ? reinterpret_cast<float*>(base + off[3]) : nullptr;
   r.saved = out->saved ? reinterpret_cast<float*>(base + off[4]) : nullptr;
   r.valid = out->valid ? reinterpret_cast<unsigned char*>(base + off[5]) : nullptr;
-  P.total_tiles = r.n_tiles;
-  P.step_budget = salf_step_budget();
-  cudaStream_t cs = static_cast<cudaStream_t>(stream);
   if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
   void* dst[6] = {out->rgb, out->depth, out->opacity, out->intensity, out->saved, out->valid};
   for (int i = 0; i < 6; ++i) {

@@ -64,3 +64,20 @@ def test_noalloc_rejects_outputs_beyond_its_fixed_staging(salf):
     with pytest.raises(salf.SalfError) as e:
         g.render_host_noalloc(big, outputs=("rgb", "depth", "opacity"))
     assert e.value.status == 1
+
+
+def test_noalloc_writes_page_locked_outputs_in_place(salf):
+    """Page-locked outputs need no staging, so even frames beyond the fixed
+    array render, equal to the device-output render bit for bit."""
+    sc = synth.random_multilevel_scene(seed=2, max_level=1)
+    g = salf.Scene(sc)
+    big = synth.pinhole(2048, 2048, 70.0, synth.camera_pose_looking((-2.2, 0.6, 1.1), 0.15))
+    R = 2048 * 2048
+    out = {"rgb": torch.empty((R, 3)).pin_memory(), "depth": torch.empty(R).pin_memory(),
+           "opacity": torch.empty(R).pin_memory()}
+    g.render_host_noalloc(big, out=out)
+    dev = g.render(big, outputs=("rgb", "depth", "opacity"))
+    torch.cuda.synchronize()
+    for k in out:
+        assert torch.equal(dev[k].cpu(), out[k]), k
+    g.check()
