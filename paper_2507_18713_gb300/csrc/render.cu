@@ -1,8 +1,7 @@
 // render.cu -- fused forward ray-cast kernel (sm_103a).
 //
-// One thread per ray, one warp per tile of 32 rays (8x4 pixels; 4 azimuths x
-// 8 beams for spinning LiDARs; 32 consecutive explicit rays), one launch for a
-// whole batch of requests (two when it mixes whole-ray and span-parallel ones).  Per ray: sensor
+// One thread per ray, one warp per 8x4 pixel tile (32 consecutive rays for
+// explicit rays), one launch for a whole batch of requests.  Per ray: sensor
 // ray generation -> traversal of the sparse voxel structure -> Eq. 1/5-6
 // density and Eq. 2 colour at each segment midpoint -> Eq. 3-4 front-to-back
 // compositing, stopping once the transmittance drops below t_min.
