@@ -12,16 +12,18 @@
 //  d sigma / d b = -a s e^{-|s|/b} / (2 b^2)) and Eq. 2 (d c / d z = c (1 - c),
 // d z / d W_c = x, d z / d W_sh = gamma).  The raydrop output adds
 // q_k = sigmoid(rho_k) and a background of 1 (T_end), and d/d rho_k =
-// w_k s (1 - s).  Gradients go to the caller's
-// input-order FP32 buffer with 16-byte vector atomics; lanes of a warp that
-// hit the same voxel in the same round stage their rows in shared memory and
-// share the summing: each adds some of the 16-byte chunks over the group, so
-// each voxel takes one set of atomics per warp and round.
+// w_k s (1 - s).  Each round, the lanes with a hit walk their rays in order
+// (T, the suffix sums and dL/dtau need it) and queue the hit's coefficients
+// in a per-warp ring in shared memory; whenever 32 are queued, the whole warp
+// builds their 32-scalar gradient rows and adds them to the caller's
+// input-order FP32 buffer with 16-byte vector atomics.  Rows of one voxel in
+// a batch are staged in shared memory and summed first, each lane adding some
+// of the 16-byte chunks, so a voxel takes one set of atomics per batch.
 #include "traverse.cuh"
 
 // warps per block and resident blocks per SM asked of the compiler
 #ifndef SALF_BWD_WARPS
-#define SALF_BWD_WARPS 8
+#define SALF_BWD_WARPS 4
 #endif
 #ifndef SALF_BWD_MIN_BLOCKS
 #define SALF_BWD_MIN_BLOCKS 1
@@ -84,6 +86,78 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
   int k = 0;
   __shared__ float s_rows[SALF_BWD_WARPS][32][33];  // padded: conflict-free columns
   float(*rows)[33] = s_rows[threadIdx.x >> 5];
+  // per-warp ring of pending hits (16 words each, padded to 17): each round's
+  // hits are queued, and the gradient rows and their atomics run 32 at a time
+  // on the whole warp
+  constexpr int QN = 64, QW = 17;
+  __shared__ float s_queue[SALF_BWD_WARPS][QN * QW];
+  float* queue = s_queue[threadIdx.x >> 5];
+  int head = 0, tail = 0;  // warp-uniform
+  const int nq = (want_int || want_drop) ? 8 : 7;
+
+  // gradient rows of n queued hits (n <= 32), summed per voxel, added to d_params
+  auto flush = [&](int n) {
+    const bool act = lane < n;
+    float gr[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) gr[q] = 0.f;
+    int key = 0;
+    if (act) {
+      const float* it = queue + ((head + lane) & (QN - 1)) * QW;
+      key = __float_as_int(it[0]);
+      const float xh[4] = {it[1], it[2], it[3], 1.f};
+      const float gm[4] = {it[12], it[13], it[14], it[15]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) gr[q] = it[4] * xh[q];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float dz = it[7 + ch];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gr[4 + 3 * ch + a] = dz * xh[a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) gr[13 + 4 * ch + b] = dz * gm[b];
+      }
+      gr[25] = it[5];
+      gr[26] = it[6];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) gr[27 + q] = it[10] * xh[q];
+      gr[31] = it[11];
+    }
+    __syncwarp();
+    const unsigned act_lanes = __ballot_sync(0xffffffffu, act);
+    if (act) {
+      const unsigned peers = __match_any_sync(act_lanes, key);
+      float4* dst = reinterpret_cast<float4*>(Q.d_params) + (size_t)key * 8;
+      if (peers == (1u << lane)) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nq)
+            atomicAdd(dst + q, make_float4(gr[4 * q], gr[4 * q + 1], gr[4 * q + 2], gr[4 * q + 3]));
+      } else {
+        // several rows of one voxel: each lane sums some 16-byte chunks over them
+#pragma unroll
+        for (int q = 0; q < 32; ++q) rows[lane][q] = gr[q];
+        __syncwarp(peers);
+        const int gn = __popc(peers), rank = __popc(peers & ((1u << lane) - 1u));
+        for (int c = rank; c < nq; c += gn) {
+          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+          unsigned m = peers;
+          while (m) {
+            const int l2 = __ffs(m) - 1;
+            m &= m - 1u;
+            sum.x += rows[l2][4 * c];
+            sum.y += rows[l2][4 * c + 1];
+            sum.z += rows[l2][4 * c + 2];
+            sum.w += rows[l2][4 * c + 3];
+          }
+          atomicAdd(dst + c, sum);
+        }
+        __syncwarp(peers);
+      }
+    }
+    head += n;
+    __syncwarp();
+  };
 
   const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   for (;;) {
@@ -108,72 +182,39 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
       const float Tn = T * e;
       const float dtau = Tn * gq - (gQ - Pk) - Tend * gbg;
       const float dsig = dtau * dl;
-
-      float gr[32];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) gr[q] = 0.f;
-      const float xh[4] = {x[0], x[1], x[2], 1.f};
+      // the hit's coefficients: the gradient row is built from them later
+      float* it = queue + ((tail + __popc(hit_lanes & ((1u << lane) - 1u))) & (QN - 1)) * QW;
+      it[0] = __int_as_float(__ldg(&S.order[h.vox]));
+      it[1] = x[0];
+      it[2] = x[1];
+      it[3] = x[2];
       if (MODE == SALF_FIELD_EXP) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gr[q] = dsig * sig * xh[q];
+        it[4] = dsig * sig;
+        it[5] = 0.f;
+        it[6] = 0.f;
       } else {
         const float a = f.a, b = f.b;
         const float ex = __expf(-fabsf(lin) / b);
-        const float ds = dsig * (a / (2.f * b)) * ex;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gr[q] = ds * xh[q];
-        gr[25] = dsig * sig / a;
-        gr[26] = -dsig * a * lin * ex / (2.f * b * b);
+        it[4] = dsig * (a / (2.f * b)) * ex;
+        it[5] = dsig * sig / a;
+        it[6] = -dsig * a * lin * ex / (2.f * b * b);
       }
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        const float dz = wgt * g[ch] * c[ch] * (1.f - c[ch]);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gr[4 + 3 * ch + a] = dz * x[a];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) gr[13 + 4 * ch + b] = dz * gam[b];
-      }
-      if (want_int) {
-        const float dz = wgt * g[5] * io * (1.f - io);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gr[27 + q] = dz * xh[q];
-      }
-      if (want_drop) gr[31] = wgt * gp * f.dr * (1.f - f.dr);
-      const int key = __ldg(&S.order[h.vox]);
-      const unsigned peers = __match_any_sync(hit_lanes, key);
-      const int nq = (want_int || want_drop) ? 8 : 7;
-      float4* dst = reinterpret_cast<float4*>(Q.d_params) + (size_t)key * 8;
-      if (peers == (1u << lane)) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < nq)
-            atomicAdd(dst + q, make_float4(gr[4 * q], gr[4 * q + 1], gr[4 * q + 2], gr[4 * q + 3]));
-      } else {
-        // several lanes hit this voxel: each sums some 16-byte chunks over the
-        // group's rows and adds them
-#pragma unroll
-        for (int q = 0; q < 32; ++q) rows[lane][q] = gr[q];
-        __syncwarp(peers);
-        const int g = __popc(peers), rank = __popc(peers & ((1u << lane) - 1u));
-        for (int c = rank; c < nq; c += g) {
-          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-          unsigned m = peers;
-          while (m) {
-            const int l2 = __ffs(m) - 1;
-            m &= m - 1u;
-            sum.x += rows[l2][4 * c];
-            sum.y += rows[l2][4 * c + 1];
-            sum.z += rows[l2][4 * c + 2];
-            sum.w += rows[l2][4 * c + 3];
-          }
-          atomicAdd(dst + c, sum);
-        }
-        __syncwarp(peers);
-      }
+      for (int ch = 0; ch < 3; ++ch) it[7 + ch] = wgt * g[ch] * c[ch] * (1.f - c[ch]);
+      it[10] = want_int ? wgt * g[5] * io * (1.f - io) : 0.f;
+      it[11] = want_drop ? wgt * gp * f.dr * (1.f - f.dr) : 0.f;
+      it[12] = gam[0];
+      it[13] = gam[1];
+      it[14] = gam[2];
+      it[15] = gam[3];
       T = Tn;
       if (++k >= nv) w.alive = false;
     }
+    tail += __popc(hit_lanes);
+    __syncwarp();
+    if (tail - head >= 32) flush(32);
   }
+  while (tail - head > 0) flush(min(32, tail - head));
 }
 
 template <int DT, int MODE>
