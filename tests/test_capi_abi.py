@@ -38,6 +38,27 @@ def test_struct_layouts_match_header():
     # kind,width,height + 7 floats = 40 -> pad to 8 -> 2*96 poses -> t0,t1 -> int + 2 floats -> ptr
     assert ctypes.sizeof(L.Sensor) == 40 + 192 + 16 + 12 + 4 + 8
     assert ctypes.sizeof(L.RasterStats) == 8 + 8 + 4 + 4 + 4 + 4
+    # kind, eta, light_dir[3], min_opacity, offset, t_far
+    assert ctypes.sizeof(L.SecondaryOpts) == 4 * 8
+
+
+def test_binding_marshals_the_new_options():
+    """ray_segments reaches salf_render_opts; rays_sensor turns an (R, 8) ray
+    tensor into an explicit-ray sensor the binding marshals as such."""
+    import torch
+    from paper_2507_18713_gb300 import _lib as L
+    from paper_2507_18713_gb300 import api
+    op = api.opts_struct(2e-4, (0.1, 0.2, 0.3), True, 5, 4)
+    assert (op.visits_cap, op.ray_segments, op.want_intensity) == (5, 4, 1)
+    assert op.t_min_transmittance == ctypes.c_float(2e-4).value   # a C float
+    rays = torch.zeros((77, 8))
+    sen = api.rays_sensor(rays)
+    assert (sen["kind"], sen["width"], sen["height"]) == ("explicit", 77, 1)
+    keep: list = []
+    s = api.sensor_struct(sen, keep)
+    assert s.kind == L.KIND["explicit"] and s.width == 77 and s.height == 1
+    assert s.rays == rays.data_ptr()
+    assert L.SECONDARY == {"reflect": 0, "refract": 1, "shadow": 2}
 
 
 def test_no_gpu_means_a_clean_error():
