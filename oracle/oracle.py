@@ -97,6 +97,9 @@ def _load():
                                        C.POINTER(_Outputs)]
             lib.orc_backward.argtypes = [vp, C.POINTER(_Sensor), C.POINTER(_Opts), vp, i64, vp,
                                          vp, vp, vp, vp, vp]
+            lib.orc_backward_bound.argtypes = lib.orc_backward.argtypes
+            lib.orc_scene_set_record.argtypes = [vp, i64, vp]
+            lib.orc_conditioned.argtypes = [vp, C.POINTER(_Sensor), vp, i64, dp, dp, vp]
             lib.orc_num_threads.restype = C.c_int
             lib.orc_subdivide_record.argtypes = [vp, i32, vp]
             lib.orc_render_actors.argtypes = [vp, vp, i32, C.POINTER(_Sensor), C.POINTER(_Opts),
@@ -143,6 +146,14 @@ class OracleScene:
     @property
     def ok(self):
         return self._h is not None
+
+    def set_record(self, v: int, rec) -> None:
+        """Replace voxel v's 32 record scalars (input order), e.g. for finite
+        differences."""
+        r = np.ascontiguousarray(np.asarray(rec, dtype=np.float64).reshape(32))
+        if _load().orc_scene_set_record(self._h, int(v), _ptr(r)) != 0:
+            raise ValueError(f"set_record({v}) rejected")
+        self._params[int(v)] = r
 
     def close(self):
         if self._h is not None:
@@ -266,6 +277,19 @@ def trace_eps(oscene, o, d, t_near, t_far, eps_abs, eps_rel, sign, cap=1 << 16,
     return ids[:n].tolist()
 
 
+def conditioned(oscene, sensor, eps_abs, eps_rel, idx=None):
+    """Per ray: True if its visit list is the same for every voxel box shrunk
+    and grown by eps_abs + eps_rel * distance (metres)."""
+    lib = _load()
+    s, keep = _sensor(sensor)
+    idx, m = _idx(sensor, idx)
+    ok = np.zeros(m, np.uint8)
+    lib.orc_conditioned(oscene._h, C.byref(s), _ptr(idx), m, float(eps_abs), float(eps_rel),
+                        _ptr(ok))
+    del keep
+    return ok.astype(bool)
+
+
 def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
            want_intensity=False, brute_force=False, visits_cap=0, max_alpha=None,
            want_raydrop=False):
@@ -303,8 +327,10 @@ def render(oscene, sensor, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
 
 def backward(oscene, sensor, g_rgb=None, g_depth=None, g_opacity=None, g_intensity=None,
              idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
-             brute_force=False, g_raydrop=None):
-    """Gradient (n, 32) of sum(g . outputs) w.r.t. every record scalar."""
+             brute_force=False, g_raydrop=None, bound=False):
+    """Gradient (n, 32) of sum(g . outputs) w.r.t. every record scalar.  With
+    bound=True, returns (gradient, rounding bound): the per-scalar magnitude
+    sum of orc_backward_bound, which an FP32 evaluation is compared against."""
     lib = _load()
     s, keep = _sensor(sensor)
     idx, m = _idx(sensor, idx)
@@ -322,6 +348,14 @@ def backward(oscene, sensor, g_rgb=None, g_depth=None, g_opacity=None, g_intensi
                           _ptr(go), _ptr(gi), _ptr(gp), _ptr(grad))
     if st != 0:
         raise RuntimeError(f"oracle backward failed: {st}")
+    if bound:
+        bnd = np.zeros((oscene.n, 32))
+        st = lib.orc_backward_bound(oscene._h, C.byref(s), C.byref(opt), _ptr(idx), m, _ptr(gr),
+                                    _ptr(gd), _ptr(go), _ptr(gi), _ptr(gp), _ptr(bnd))
+        if st != 0:
+            raise RuntimeError(f"oracle backward bound failed: {st}")
+        del keep
+        return grad, bnd
     del keep
     return grad
 

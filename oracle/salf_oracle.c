@@ -145,6 +145,13 @@ int orc_scene_create(const orc_scene_desc* d, orc_scene** out) {
   return 0;
 }
 
+int orc_scene_set_record(orc_scene* s, int64_t v, const double* rec) {
+  if (!s || v < 0 || v >= s->n || !rec) return 1;
+  if (s->mode == 1 && !(rec[25] > 0 && rec[26] > 0)) return 1;
+  memcpy(s->params + (size_t)REC * v, rec, REC * sizeof(double));
+  return 0;
+}
+
 static void voxel_box(const orc_scene* s, int64_t v, double lo[3], double hi[3], double* edge) {
   int32_t l = s->level[v];
   double e = s->s0 / (double)(1 << l);
@@ -585,6 +592,59 @@ int orc_gen_rays(const orc_sensor* sen, const int64_t* idx, int64_t m, double* o
 /* Local fields (Eq. 1, 2, 5, 6)                                             */
 /* ------------------------------------------------------------------------ */
 
+/* Per ray of a sensor (idx as for orc_render): 1 if the ordered list of
+ * voxels crossed with positive length is the same for every box shrunk and
+ * grown by eps_abs + eps_rel * (distance of the box centre), else 0 (also 0
+ * for invalid rays).  Such a list does not change under position errors
+ * below that margin. */
+int orc_conditioned(const orc_scene* s, const orc_sensor* sen, const int64_t* idx, int64_t m,
+                    double eps_abs, double eps_rel, uint8_t* ok) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t r = idx ? idx[i] : i;
+    double o[3], d[3], tn, tf, tau;
+    uint8_t valid;
+    one_ray(sen, r, o, d, &tn, &tf, &tau, &valid);
+    ok[i] = 0;
+    if (!valid) continue;
+    ivec cand = {0, 0, 0};
+    if (s->n <= 20000) {
+      for (int64_t v = 0; v < s->n; ++v) iv_push(&cand, (int32_t)v);
+    } else {
+      dda_candidates(s, o, d, tn, tf, 1, &cand);
+      unique_ids(&cand);
+    }
+    hitvec hv[2] = {{0, 0, 0}, {0, 0, 0}};
+    for (int side = 0; side < 2; ++side) {
+      const double sign = side ? 1.0 : -1.0;
+      for (int64_t c = 0; c < cand.n; ++c) {
+        int32_t v = cand.v[c];
+        double lo[3], hi[3], e, a, b, dist = 0;
+        voxel_box(s, v, lo, hi, &e);
+        for (int ax = 0; ax < 3; ++ax) {
+          double cc = 0.5 * (lo[ax] + hi[ax]) - o[ax];
+          dist += cc * cc;
+        }
+        double eps = eps_abs + eps_rel * sqrt(dist);
+        for (int ax = 0; ax < 3; ++ax) {
+          lo[ax] -= sign * eps;
+          hi[ax] += sign * eps;
+        }
+        if (slab(lo, hi, o, d, &a, &b) && dmin(b, tf) - dmax(a, tn) > s->min_len)
+          hv_push(&hv[side], v, a, b);
+      }
+      sort_hits(&hv[side], tn);
+    }
+    int same = hv[0].n == hv[1].n;
+    for (int64_t k = 0; same && k < hv[0].n; ++k) same = hv[0].h[k].voxel == hv[1].h[k].voxel;
+    ok[i] = (uint8_t)same;
+    free(hv[0].h);
+    free(hv[1].h);
+    free(cand.v);
+  }
+  return 0;
+}
+
 void orc_sh_basis(const double dir[3], double g[4]) {
   const double C0 = 0.5 / sqrt(M_PI);
   const double C1 = 0.5 * sqrt(3.0 / M_PI);
@@ -860,6 +920,132 @@ int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
     }
     free(gq);
     free(suf);
+    rr_free(&rr);
+  }
+  return 0;
+}
+
+/* Rounding bound for an FP32 evaluation of orc_backward's sum (not part of
+ * the method: a tolerance for comparing an FP32 implementation with this FP64
+ * adjoint).  bound (n*32, input order) += per record scalar, over the same
+ * rays and hits as orc_backward, the magnitude of each hit's contribution
+ * with
+ *   - every factor in absolute value and every cancelling sum (the suffix
+ *     sums of dL/dtau, g . q) replaced by the sum of its terms' absolute
+ *     values;
+ *   - the conditioning of the hit's geometry folded in: a position carried
+ *     in FP32 relative to the sensor is off by about u t (u the unit
+ *     roundoff, t the distance), i.e. by u kappa in local coordinates with
+ *     kappa = 1 + 2 t / edge, which moves every field of the voxel by up to
+ *     u kappa times its slopes' L1 norm; so a relative factor
+ *     Phi = kappa (1 + |slopes|_1) + Lambda, where Lambda = sum over the
+ *     ray's hits of (sigma t + tau kappa |W_sigma slopes|_1) bounds the
+ *     relative error of any transmittance of the ray in units of u;
+ *   - terms proportional to the segment length delta carry its absolute
+ *     error u t: a weight w = T (1 - e^{-sigma delta}) becomes
+ *     w Phi + T sigma t, and dL/dsigma = dL/dtau delta becomes
+ *     |dL/dtau| (delta Phi + t);
+ *   - a local-coordinate factor x_a becomes |x_a| + 1 (its absolute error
+ *     u kappa is not relative to x_a, which may be exactly 0).
+ * An FP32 evaluation in the same order of operations is then expected within
+ * a small multiple of u times this bound (plus its own relative rounding). */
+int orc_backward_bound(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
+                       const int64_t* idx, int64_t m, const double* g_rgb, const double* g_depth,
+                       const double* g_opacity, const double* g_intensity,
+                       const double* g_raydrop, double* bound) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t r = idx ? idx[i] : i;
+    double o[3], d[3], tn, tf, tau;
+    uint8_t valid;
+    one_ray(sen, r, o, d, &tn, &tf, &tau, &valid);
+    if (!valid) continue;
+    double gc[3] = {0, 0, 0}, gd = 0, go = 0, gi = 0;
+    if (g_rgb)
+      for (int q = 0; q < 3; ++q) gc[q] = g_rgb[3 * i + q];
+    if (g_depth) gd = g_depth[i];
+    if (g_opacity) go = g_opacity[i];
+    if (g_intensity && opt->want_intensity) gi = g_intensity[i];
+    double gp = (g_raydrop && opt->want_raydrop) ? g_raydrop[i] : 0.0;
+    ray_record rr;
+    memset(&rr, 0, sizeof(rr));
+    composite_ray(s, opt, o, d, tn, tf, &rr);
+    int64_t n = rr.n;
+    size_t N = (size_t)(n ? n : 1);
+    double* gqa = (double*)malloc(N * sizeof(double));
+    double* kap = (double*)malloc(N * sizeof(double));
+    double* phi = (double*)malloc(N * sizeof(double));
+    double* tk = (double*)malloc(N * sizeof(double));
+    double* wm = (double*)malloc(N * sizeof(double));
+    double lam = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      int32_t v = rr.vox[k];
+      const double* rec = s->params + (size_t)REC * v;
+      double lo[3], hi[3], e;
+      voxel_box(s, v, lo, hi, &e);
+      tk[k] = rr.tm[k] + 0.5 * rr.dl[k];
+      kap[k] = 1.0 + 2.0 * tk[k] / e;
+      double ws = fabs(rec[0]) + fabs(rec[1]) + fabs(rec[2]);
+      lam += rr.sig[k] * tk[k] + rr.sig[k] * rr.dl[k] * kap[k] * ws;
+      gqa[k] = fabs(gc[0] * rr.c[3 * k]) + fabs(gc[1] * rr.c[3 * k + 1]) +
+               fabs(gc[2] * rr.c[3 * k + 2]) + fabs(gd * rr.tm[k]) + fabs(go) +
+               fabs(gi * rr.io[k]) + fabs(gp * rr.dr[k]);
+    }
+    double sabs = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      int32_t v = rr.vox[k];
+      const double* rec = s->params + (size_t)REC * v;
+      double sl = 0.0;
+      for (int q = 0; q < 3; ++q) sl += fabs(rec[q]);
+      for (int q = 4; q < 13; ++q) sl += fabs(rec[q]);
+      for (int q = 27; q < 30; ++q) sl += fabs(rec[q]);
+      phi[k] = kap[k] * (1.0 + sl) + lam;
+      wm[k] = rr.w[k] * phi[k] + rr.T[k] * rr.sig[k] * tk[k];
+      sabs += wm[k] * gqa[k];
+    }
+    double gbga = fabs(gc[0] * opt->background[0]) + fabs(gc[1] * opt->background[1]) +
+                  fabs(gc[2] * opt->background[2]) + fabs(gp);
+    double gam[4];
+    orc_sh_basis(d, gam);
+    for (int64_t k = 0; k < n; ++k) {
+      int32_t v = rr.vox[k];
+      const double* rec = s->params + (size_t)REC * v;
+      double* bd = bound + (size_t)REC * v;
+      double dtm = rr.T[k] * gqa[k] + sabs + rr.t_end * gbga;
+      double dsm = dtm * (rr.dl[k] * phi[k] + tk[k]);
+      const double* x = rr.x + 3 * k;
+      double xa[4] = {fabs(x[0]) + 1.0, fabs(x[1]) + 1.0, fabs(x[2]) + 1.0, 2.0};
+      if (s->mode == 0) {
+        for (int a = 0; a < 4; ++a) ADD(&bd[a], dsm * rr.sig[k] * xa[a]);
+      } else {
+        double a = rec[25], b = rec[26], sp = rr.lin[k];
+        double ex = exp(-fabs(sp) / b);
+        double ds = dsm * (a / (2.0 * b)) * ex * (1.0 + kap[k] / b);
+        for (int q = 0; q < 4; ++q) ADD(&bd[q], ds * xa[q]);
+        ADD(&bd[25], dsm * rr.sig[k] / a);
+        ADD(&bd[26], dsm * a * (fabs(sp) + 1.0) * ex / (2.0 * b * b) * (1.0 + kap[k] / b));
+      }
+      for (int q = 0; q < 3; ++q) {
+        double cq = rr.c[3 * k + q];
+        double dz = wm[k] * fabs(gc[q]) * cq * (1.0 - cq);
+        for (int a = 0; a < 3; ++a) ADD(&bd[4 + 3 * q + a], dz * xa[a]);
+        for (int b = 0; b < 4; ++b) ADD(&bd[13 + 4 * q + b], dz * fabs(gam[b]));
+      }
+      if (opt->want_intensity) {
+        double io = rr.io[k];
+        double dz = wm[k] * fabs(gi) * io * (1.0 - io);
+        for (int a = 0; a < 4; ++a) ADD(&bd[27 + a], dz * xa[a]);
+      }
+      if (opt->want_raydrop) {
+        double dr = rr.dr[k];
+        ADD(&bd[31], wm[k] * fabs(gp) * dr * (1.0 - dr));
+      }
+    }
+    free(gqa);
+    free(kap);
+    free(phi);
+    free(tk);
+    free(wm);
     rr_free(&rr);
   }
   return 0;

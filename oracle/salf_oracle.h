@@ -87,6 +87,9 @@ typedef struct {
 int orc_scene_create(const orc_scene_desc* desc, orc_scene** out);
 void orc_scene_free(orc_scene* s);
 int64_t orc_scene_lookup(const orc_scene* s, int32_t level, int32_t i, int32_t j, int32_t k);
+/* Replace voxel v's 32 record scalars (input order; for finite differences).
+ * Status 1 if v is out of range or an SDF record has a <= 0 or b <= 0. */
+int orc_scene_set_record(orc_scene* s, int64_t v, const double* rec);
 
 /* Rays for the given ray indices (idx NULL: all rays 0..m-1). */
 int orc_gen_rays(const orc_sensor* sen, const int64_t* idx, int64_t m, double* o, double* d,
@@ -107,6 +110,11 @@ int64_t orc_trace_eps(const orc_scene* s, const double o[3], const double d[3], 
                       double tf, double eps_abs, double eps_rel, int32_t sign, int32_t* ids,
                       double* t_in, double* t_out, int64_t cap);
 
+/* Per ray (idx NULL: all rays 0..m-1): 1 if its visit list is the same for
+ * every voxel box shrunk and grown by eps_abs + eps_rel * |box centre - o|. */
+int orc_conditioned(const orc_scene* s, const orc_sensor* sen, const int64_t* idx, int64_t m,
+                    double eps_abs, double eps_rel, uint8_t* ok);
+
 int orc_render(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
                const int64_t* idx, int64_t m, const orc_outputs* out);
 /* grad (n*32, input order) += d/dparams of
@@ -117,6 +125,15 @@ int orc_backward(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
                  const int64_t* idx, int64_t m, const double* g_rgb, const double* g_depth,
                  const double* g_opacity, const double* g_intensity, const double* g_raydrop,
                  double* grad);
+/* A rounding bound for FP32 evaluations of orc_backward's gradient (same
+ * arguments): bound (n*32) += per scalar the magnitude of every contribution
+ * with absolute factors, absolute-term sums and the hit geometry's FP32
+ * conditioning folded in (see the definition).  A tolerance, not part of
+ * the method. */
+int orc_backward_bound(const orc_scene* s, const orc_sensor* sen, const orc_opts* opt,
+                       const int64_t* idx, int64_t m, const double* g_rgb, const double* g_depth,
+                       const double* g_opacity, const double* g_intensity,
+                       const double* g_raydrop, double* bound);
 int orc_num_threads(void);
 
 /* Sec. III-C densification: the record of child `child` (bits x | y << 1 |

@@ -127,3 +127,19 @@ def check_visits(oracle, osc, sensor, scene, g_vis, g_cnt, o_vis, o_cnt, idx):
         for a, c in zip(gl, gl[1:]):
             assert g_in[pos[a]] <= g_out[pos[c]], (ray_id, gl, grown)
     return len(g_cnt), len(bad)
+
+
+def conditioned_rays(oracle, osc, sensor, idx, scene, t_min=0.0, term_gap_min=1e-3):
+    """Oracle-chosen mask over the rays `idx`: True where the ray's visit list
+    is the same for every voxel box shrunk and grown by the visit-list margin
+    (EPS_ABS_CELLS finest edges + EPS_REL x distance), and, with early
+    termination, its transmittance never came within exp(term_gap_min) of
+    t_min at a termination test.  Rays outside the mask have a visit list (or
+    a composited count) that FP32 rounding may legitimately change; gradient
+    checks give them zero output gradient.  Oracle-only."""
+    sf = scene.s0 / (1 << scene.max_level)
+    ok = oracle.conditioned(osc, sensor, EPS_ABS_CELLS * sf, EPS_REL, idx)
+    if t_min > 0:
+        r = oracle.render(osc, sensor, idx=idx, t_min=t_min)
+        ok &= r["term_gap"] > term_gap_min
+    return ok

@@ -538,3 +538,73 @@ def test_dda_candidates_equal_brute_force_deep_octree(oracle_lib):
             a = oracle_lib.trace(osc, o, d, brute_force=True)
             b = oracle_lib.trace(osc, o, d, brute_force=False)
             assert [h[0] for h in a] == [h[0] for h in b]
+
+
+def test_backward_bound_dominates_the_gradient_and_scales_with_it(oracle_lib):
+    """orc_backward_bound is a sum of contribution magnitudes, each at least
+    the contribution's absolute value: it bounds |gradient| per scalar, is
+    zero exactly where no hit contributes, does not depend on the sign of
+    the output gradients and scales linearly with their size."""
+    for mode in ("exp", "sdf"):
+        sc = synth.random_multilevel_scene(seed=12, max_level=2, dims=(4, 3, 3), p_occ=0.8,
+                                           mode=mode)
+        cam = synth.pinhole(12, 9, 70.0, synth.camera_pose_looking((-1.9, 0.25, 0.9), 0.1))
+        R = 12 * 9
+        rng = np.random.default_rng(5)
+        g = dict(g_rgb=rng.normal(size=(R, 3)), g_depth=rng.normal(size=R),
+                 g_opacity=rng.normal(size=R), g_intensity=rng.normal(size=R))
+        kw = dict(t_min=1e-3, background=(0.3, 0.1, 0.7), want_intensity=True, brute_force=True)
+        osc = oracle_lib.OracleScene(sc)
+        grad, bnd = oracle_lib.backward(osc, cam, **g, **kw, bound=True)
+        assert np.all(bnd >= np.abs(grad))
+        touched = np.abs(grad).sum(1) > 0
+        assert np.all(bnd[grad != 0] > 0)
+        assert np.all(bnd[~touched] == 0)
+        assert np.all(bnd[:, 31] == 0)
+        _, b2 = oracle_lib.backward(osc, cam, **{k: -2.0 * v for k, v in g.items()}, **kw,
+                                    bound=True)
+        assert np.allclose(b2, 2.0 * bnd, rtol=1e-12, atol=0)
+
+
+def test_set_record_equals_a_scene_built_with_that_record(oracle_lib):
+    sc = synth.random_multilevel_scene(seed=7, max_level=1, dims=(4, 3, 3), p_occ=0.8)
+    cam = synth.pinhole(16, 12, 70.0, synth.camera_pose_looking((-1.9, 0.25, 0.9), 0.1))
+    osc = oracle_lib.OracleScene(sc)
+    rec = np.random.default_rng(1).normal(size=32)
+    osc.set_record(3, rec)
+    p = sc.params.astype(np.float64).copy()
+    p[3] = rec
+    ref = oracle_lib.render(oracle_lib.OracleScene(sc, params=p), cam, t_min=0.0,
+                            brute_force=True)
+    got = oracle_lib.render(osc, cam, t_min=0.0, brute_force=True)
+    for k in ("rgb", "depth", "opacity"):
+        assert np.array_equal(got[k], ref[k])
+    with pytest.raises(ValueError):
+        osc.set_record(sc.n, rec)
+
+
+def test_conditioned_rays(oracle_lib):
+    """A ray through the middle of a row of cells is conditioned; rays along a
+    cell plane or through a cell edge are not; and the C check agrees with
+    comparing the shrunk and grown visit lists one ray at a time."""
+    sc = synth.random_multilevel_scene(seed=2, max_level=1, dims=(4, 4, 4), p_occ=1.0)
+    osc = oracle_lib.OracleScene(sc)
+    o = np.array(sc.origin, dtype=np.float64)
+    s0 = sc.s0
+    rows = np.array([
+        [*(o + [-1.0, 0.3 * s0, 0.3 * s0]), 1, 0, 0, 0.0, 0.0],   # inside a row of cells
+        [*(o + [-1.0, 1.0 * s0, 0.3 * s0]), 1, 0, 0, 0.0, 0.0],   # in the plane y = s0
+        [*(o + [-1.0, 2.0 * s0, 2.0 * s0]), 1, 0, 0, 0.0, 0.0],   # along a cell edge
+    ])
+    sen = synth.explicit_rays(rows, np.float64)
+    ok = oracle_lib.conditioned(osc, sen, 1e-6, 1e-6)
+    assert ok.tolist() == [True, False, False]
+    cam = synth.pinhole(24, 18, 70.0, synth.camera_pose_looking((-1.9, 0.25, 0.9), 0.1))
+    ok = oracle_lib.conditioned(osc, cam, 1e-4 * s0 / 2, 4e-6)
+    rays = oracle_lib.gen_rays(cam)
+    for i in range(0, 24 * 18, 7):
+        a = oracle_lib.trace_eps(osc, rays["o"][i], rays["d"][i], rays["t_near"][i],
+                                 rays["t_far"][i], 1e-4 * s0 / 2, 4e-6, -1)
+        b = oracle_lib.trace_eps(osc, rays["o"][i], rays["d"][i], rays["t_near"][i],
+                                 rays["t_far"][i], 1e-4 * s0 / 2, 4e-6, +1)
+        assert ok[i] == (a == b)
