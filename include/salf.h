@@ -263,17 +263,19 @@ salf_status salf_render_rays(salf_scene* scene, const salf_sensor* sensor,
  * on_host = 1 grows a staging buffer with cudaMalloc instead.)
  * Page-locked host buffers the device can address (cudaHostAlloc /
  * cudaHostRegister; saved 16-byte aligned) are written by the kernel in place.
- * Other buffers are staged in a fixed 48 MiB array compiled into the library
- * (every device that loads the library holds it until the process exits);
+ * Other buffers are staged in a fixed 48 MiB array compiled into the library;
  * requests whose outputs need more staging than that are rejected with
- * SALF_ERR_INVALID.  `out` holds host pointers (on_host is ignored); the
- * debug outputs (visits, visit_count, ray_dump, steps) are not supported;
- * explicit rays must be device memory.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Calls on one device share
- * the array: two calls that overlap on the GPU (e.g. from two host threads)
- * race, so serialise them.  Synchronous: returns after the outputs are in the
- * host buffers.  Calls no cudaMalloc, cudaFree or allocating routine.
+ * SALF_ERR_INVALID.  salf_create resolves the array on its device (with
+ * lazy module loading, that is when the device allocates it), so the array
+ * is resident from the first salf_create on a device until the process
+ * exits: a caller that reserves device memory in its own pool does so after
+ * salf_create.  `out` holds host pointers (on_host is ignored); the debug
+ * outputs (visits, visit_count, ray_dump, steps), max_alpha and raydrop are
+ * not supported (SALF_ERR_INVALID); explicit rays must be device memory.
+ * Calls on one device share the array: two calls that overlap on the GPU
+ * (e.g. from two host threads) race, so serialise them.  Synchronous:
+ * returns after the outputs are in the host buffers.  Calls no cudaMalloc,
+ * cudaFree or allocating routine.
  */
 salf_status salf_render_rays_host_noalloc(salf_scene* scene, const salf_sensor* sensor,
                                           const salf_render_opts* opts,

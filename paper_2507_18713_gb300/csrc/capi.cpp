@@ -37,6 +37,9 @@ extern "C" salf_status salf_create(int32_t device, salf_ctx** out) {
     return SALF_ERR_INVALID;
   }
   if ((e = cudaSetDevice(device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  // the no-alloc entry point's fixed staging array becomes resident here
+  const salf_status st = salf_noalloc_setup(device);
+  if (st != SALF_OK) return st;
   salf_ctx* c = new salf_ctx();
   c->device = device;
   *out = c;

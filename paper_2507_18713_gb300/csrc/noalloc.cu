@@ -9,13 +9,15 @@
 // acceptable, host applications whose device memory is reserved up front by
 // their own pooling allocator, and plug-ins that their host forbids to
 // allocate.  This entry point stages the outputs in a fixed array compiled
-// into the library instead (SALF_NOALLOC_STAGING_BYTES, held by every device
-// that loads the library until the process exits).  It calls no cudaMalloc,
-// cudaFree or allocating library routine.
+// into the library instead (SALF_NOALLOC_STAGING_BYTES).  It calls no
+// cudaMalloc, cudaFree or allocating library routine.
 //
-// The device address of the array is looked up with cudaGetSymbolAddress the
-// first time the entry point runs on a device (with that device current) and
-// cached per device; that first call should come before any stream capture.
+// The array's device address is looked up with cudaGetSymbolAddress by
+// salf_create, once per device, with that device current, and cached.  Under
+// lazy module loading (the CUDA default) that lookup is also what loads this
+// file's module and so makes the device hold the array: it is resident from
+// the first salf_create on a device until the process exits, and a caller
+// that reserves device memory in its own pool does so after salf_create.
 // Every call on a device shares the array and leaves its contents behind; the
 // forward kernel overwrites every output element it stages, so nothing needs
 // clearing between calls.  Two calls that overlap on the GPU (for instance
@@ -39,7 +41,7 @@ char* g_staging_ptr[SALF_NOALLOC_MAX_DEVICES] = {};
 salf_status staging_for_device(int device, char** out) {
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (device < 0 || device >= SALF_NOALLOC_MAX_DEVICES) {
-    salf_set_error("salf_render_rays_host_noalloc: device index out of range");
+    salf_set_error("no-alloc staging: device index out of range");
     return SALF_ERR_INVALID;
   }
   if (!g_staging_ptr[device]) {
@@ -55,6 +57,14 @@ salf_status staging_for_device(int device, char** out) {
 size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
 }  // namespace
 
+// Called by salf_create with `device` current: resolves (and, under lazy
+// module loading, loads) the staging array, so that later no-alloc calls on
+// the device find it resident.
+salf_status salf_noalloc_setup(int device) {
+  char* base = nullptr;
+  return staging_for_device(device, &base);
+}
+
 extern "C" salf_status salf_render_rays_host_noalloc(salf_scene* sc, const salf_sensor* sen,
                                                      const salf_render_opts* opts,
                                                      const salf_outputs* out, void* stream) {
@@ -63,8 +73,9 @@ extern "C" salf_status salf_render_rays_host_noalloc(salf_scene* sc, const salf_
     return SALF_ERR_INVALID;
   }
   if (out->visits || out->visit_count || out->ray_dump || out->steps || out->raydrop ||
-      (opts && opts->visits_cap > 0)) {
-    salf_set_error("salf_render_rays_host_noalloc: debug and raydrop outputs are not supported");
+      out->max_alpha || (opts && opts->visits_cap > 0)) {
+    salf_set_error("salf_render_rays_host_noalloc: debug, alpha-maxima and raydrop outputs are "
+                   "not supported");
     return SALF_ERR_INVALID;
   }
   if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid) {

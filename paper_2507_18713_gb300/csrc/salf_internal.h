@@ -223,6 +223,8 @@ struct salf_scene {
 // Implemented in the .cu / .cpp files of the library.
 void salf_set_error(const std::string& msg);
 salf_status salf_cuda_fail(cudaError_t e, const char* what);
+// Resolve the no-alloc entry point's staging array on `device` (current).
+salf_status salf_noalloc_setup(int device);
 salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_scene** out);
 // The same build from device-resident level / ijk / params (validated by the caller).
 salf_status salf_build_scene_gpu(salf_ctx* ctx, const salf_scene_desc* d, salf_scene** out);

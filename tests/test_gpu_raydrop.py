@@ -8,6 +8,7 @@ import pytest
 
 import synth
 from tests.parity_util import TOL_C, to_np
+from tests.parity_util import conditioned_rays
 from tests.test_gpu_backward import grad_close
 
 pytestmark = pytest.mark.gpu
@@ -92,18 +93,19 @@ def test_raydrop_adjoint_matches_oracle(salf, oracle_lib, mode):
                       synth.lidar_pose((0.6, 0.6, 0.9), 0.3), t0=0.0, t1=0.1)
     R = 12 * 48
     rng = np.random.default_rng(1)
-    gp = rng.normal(size=R).astype(np.float32)
-    gd = (rng.normal(size=R) * 0.1).astype(np.float32)
+    keep = conditioned_rays(oracle_lib, osc, sen, None, sc)
+    gp = rng.normal(size=R).astype(np.float32) * keep
+    gd = (rng.normal(size=R) * 0.1).astype(np.float32) * keep
     kw = dict(t_min=0.0, want_intensity=True)
     out = g.render(sen, saved=True, outputs=("raydrop", "depth"), **kw)
     T = lambda a: torch.from_numpy(a).cuda()
     dg = g.backward(sen, out["saved"], d_depth=T(gd), raydrop=out["raydrop"], d_raydrop=T(gp),
                     **kw)
     torch.cuda.synchronize()
-    do = oracle_lib.backward(osc, sen, g_depth=gd.astype(np.float64),
-                             g_raydrop=gp.astype(np.float64), **kw)
+    do, bnd = oracle_lib.backward(osc, sen, g_depth=gd.astype(np.float64),
+                                  g_raydrop=gp.astype(np.float64), bound=True, **kw)
     assert np.abs(do[:, 31]).max() > 0
-    grad_close(dg.cpu().numpy(), do)
+    grad_close(dg.cpu().numpy(), do, bnd)
     g.check()
 
 

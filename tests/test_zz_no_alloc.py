@@ -57,6 +57,50 @@ def test_noalloc_matches_regular_entry_point_on_two_calls_in_a_row(salf):
             assert np.abs(got["intensity"] - ref["intensity"]).max() <= TOL_C
 
 
+def test_noalloc_leaves_device_memory_unchanged(salf):
+    """The point of the entry point: once a call of each sensor kind has run
+    (loading its kernels), staged calls of other sizes change neither the
+    device's free memory nor the scene's device footprint (no staging
+    buffer is created for them)."""
+    sc = synth.random_multilevel_scene(seed=2, max_level=2, dims=(6, 5, 4), p_occ=0.7)
+    g = salf.Scene(sc)
+    lid = lambda b, a: synth.lidar(b, a, synth.lidar_pose((0.35, 0.55, 1.05), 0.2),
+                                   synth.lidar_pose((0.95, 0.7, 1.05), 0.45), t0=0.0, t1=0.1)
+    pin = lambda w, h: synth.pinhole(w, h, 70.0, synth.camera_pose_looking((-2.2, 0.6, 1.1), 0.15))
+    for sen, wi in ((pin(160, 120), False), (lid(32, 512), True)):
+        g.render_host_noalloc(sen, want_intensity=wi, outputs=("rgb", "depth", "opacity", "valid")
+                              if not wi else ("depth", "opacity", "intensity", "valid"))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    bytes0 = g.info()["device_bytes"]
+    for sen, wi in ((pin(1024, 768), False), (lid(64, 1024), True), (pin(320, 200), False)):
+        g.render_host_noalloc(sen, want_intensity=wi, outputs=("rgb", "depth", "opacity", "valid")
+                              if not wi else ("depth", "opacity", "intensity", "valid"))
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert g.info()["device_bytes"] == bytes0
+
+
+def test_noalloc_rejects_alpha_maxima(salf):
+    import ctypes as C
+    from paper_2507_18713_gb300 import _lib as L
+    from paper_2507_18713_gb300.api import opts_struct, sensor_struct
+    sc = synth.random_multilevel_scene(seed=2, max_level=1)
+    g = salf.Scene(sc)
+    cam = synth.pinhole(32, 24, 70.0, synth.camera_pose_looking((-2.2, 0.6, 1.1), 0.15))
+    ma = torch.zeros(sc.n, device="cuda")
+    depth = torch.empty(32 * 24)
+    o = L.Outputs()
+    o.depth = depth.data_ptr()
+    o.max_alpha = ma.data_ptr()
+    keep = []
+    s = sensor_struct(cam, keep)
+    op = opts_struct()
+    st = L.load().salf_render_rays_host_noalloc(g._h, C.byref(s), C.byref(op), C.byref(o), None)
+    assert st == L.ERR_INVALID
+
+
 def test_noalloc_rejects_outputs_beyond_its_fixed_staging(salf):
     sc = synth.random_multilevel_scene(seed=2, max_level=1)
     g = salf.Scene(sc)
