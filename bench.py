@@ -231,7 +231,7 @@ def section(torch, P, gscene, sensor, steps, warmup, flush, b_field, b_out, want
 
 # --------------------------------------------------------------------- extras
 
-def bench_backward(torch, P, steps, warmup, flush):
+def bench_backward(torch, P, steps, warmup, flush, peak):
     sc = synth.driving_scene(1_000_000, seed=4, ground_extent=141.4, n_actors=140)
     g = P.Scene(sc, dtype="bf16")
     cams = [synth.pinhole(960, 640, 60.0, synth.camera_pose_looking(
@@ -255,9 +255,34 @@ def bench_backward(torch, P, steps, warmup, flush):
     ms = timed_renders(torch, step, max(3, steps // 20), warmup, flush)
     g.check()
     avg = sum(ms) / len(ms)
+    # the adjoint kernel alone (one launch per camera), with its algorithmic
+    # bytes: per visit the BF16 record's 25 used scalars (50 B) and 25 FP32
+    # gradient scalars added (100 B); per ray dL/drgb (12 B) and the saved
+    # totals (32 B)
+    grads = [(o["rgb"] - tg).mul_(2 * inv) for o, tg in zip(outs, targets)]
+    visits = sum(int(o["saved"][:, 7].double().sum().item()) for o in outs)
+    k = [0]
+
+    def adj():
+        i = k[0] % len(cams)
+        k[0] += 1
+        g.backward(cams[i], outs[i]["saved"], d_rgb=grads[i], d_params=dparams)
+
+    ms_adj = timed_renders(torch, adj, 8 * max(3, steps // 20), warmup, flush)
+    avg_adj = sum(ms_adj) / len(ms_adj)
+    b_adj = visits / len(cams) * (B_FIELD_EXP_BF16 + 4 * 25) + R * (12 + 32)
+    ach = b_adj / (avg_adj * 1e-3) / 1e9
     return dict(workload="8 pinhole 960x640, driving scene 1,000,000 voxels (seed 4), BF16 "
                 "records, FP32 grads, MSE vs U[0,1] targets",
-                ms_per_step=avg, mrays_s=len(cams) * R / (avg * 1e-3) / 1e6)
+                ms_per_step=avg, mrays_s=len(cams) * R / (avg * 1e-3) / 1e6,
+                adjoint=dict(kernel="k_backward<BF16,EXP>", ms_per_camera=avg_adj,
+                             visits_per_ray=visits / (len(cams) * R),
+                             roofline=dict(bound="hbm", achieved=ach, peak=peak, unit="GB/s",
+                                           frac=ach / peak, bytes_per_launch=b_adj,
+                                           note="per visit 50 B BF16 record + 100 B of gradient "
+                                                "scalars (25 x 4 B), per ray 12 B dL/drgb + "
+                                                "32 B saved totals; visits counted by the "
+                                                "forward kernel")))
 
 
 def bench_refine(torch, P, flush):
@@ -312,7 +337,7 @@ def bench_refine(torch, P, flush):
                      "= salf_build_scene from the device-resident voxel list (device build)")
 
 
-def bench_serving(torch, P, duration_s=5.0, seed=6):
+def bench_serving(torch, P, duration_s=10.0, seed=6, n_streams=4):
     sc = synth.driving_scene(4_000_000, seed=3, ground_layers=2, n_actors=600)
     g = P.Scene(sc, dtype="bf16")
     rng = np.random.default_rng(seed)
@@ -342,13 +367,13 @@ def bench_serving(torch, P, duration_s=5.0, seed=6):
     reqs = [(t, make(si)) for t, si in events]
     total_rays = sum(s["width"] * s["height"] for _, s in reqs)
     # continuous batching
-    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=2)
+    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=n_streams)
     warm = [srv.submit(s, want_intensity=s["kind"] == "lidar") for _, s in reqs[:8]]
     for t in warm:
         srv.poll(t, -1)
         srv.release(t)
     srv.close()
-    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=2)
+    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=n_streams)
     import queue
     q: "queue.Queue" = queue.Queue()
 
@@ -387,7 +412,7 @@ def bench_serving(torch, P, duration_s=5.0, seed=6):
     # saturation: the same requests offered all at once (closed loop)
     sat = reqs[:min(len(reqs), 400)]
     sat_rays = sum(s["width"] * s["height"] for _, s in sat)
-    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=2)
+    srv = P.Server(g, mem_budget_bytes=2 << 30, n_streams=n_streams)
     q2: "queue.Queue" = queue.Queue()
 
     def consumer2():
@@ -420,13 +445,20 @@ def bench_serving(torch, P, duration_s=5.0, seed=6):
     return dict(workload=f"20 sensors at 10 Hz Poisson for {duration_s:.0f} s, driving scene "
                 "4,000,000 voxels (seed 3), BF16 records", requests=len(reqs),
                 offered_mrays_s=total_rays / duration_s / 1e6,
+                streams=n_streams,
                 batched=dict(p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], launches=st["launches"],
+                             requests_per_launch=st["requests_launched"] / max(1, st["launches"]),
+                             max_batch=st["max_batch"], mixed_launches=st["mixed_launches"],
                              mrays_s=total_rays / t_end / 1e6, wall_s=t_end),
                 sequential=dict(p50_ms=q(0.5), p99_ms=q(0.99), mrays_s=total_rays / t_seq / 1e6,
                                 wall_s=t_seq),
                 saturated=dict(requests=len(sat), rays=sat_rays,
                                batched_mrays_s=sat_rays / t_sat_b / 1e6,
                                batched_launches=st_sat["launches"],
+                               requests_per_launch=st_sat["requests_launched"]
+                               / max(1, st_sat["launches"]),
+                               mixed_launches=st_sat["mixed_launches"],
+                               batched_p50_ms=st_sat["p50_ms"], batched_p99_ms=st_sat["p99_ms"],
                                sequential_mrays_s=sat_rays / t_sat_s / 1e6,
                                note="all requests offered at once; sequential = one "
                                     "salf_render_rays per request in arrival order, "
@@ -435,13 +467,52 @@ def bench_serving(torch, P, duration_s=5.0, seed=6):
 
 # --------------------------------------------------------------------- oracle
 
-def oracle_rate(scene_or, sensor, n_sample, seed):
+def oracle_rate(scene_or, sensor, n_sample, seed, outputs=None):
+    """Rays per second of the oracle on the host cores; `outputs`, if a dict,
+    receives the rendered rays (idx) and their outputs."""
     import oracle
-    idx = synth.sample_ray_indices(sensor["width"] * sensor["height"], n_sample, seed)
+    R = sensor["width"] * sensor["height"]
+    n_sample = min(n_sample, R)
+    idx = None if n_sample >= R else synth.sample_ray_indices(R, n_sample, seed)
     t = time.perf_counter()
-    oracle.render(scene_or, sensor, idx=idx)
+    out = oracle.render(scene_or, sensor, idx=idx)
     dt = time.perf_counter() - t
+    if outputs is not None:
+        outputs.update(out, idx=np.arange(R) if idx is None else idx)
     return n_sample / dt / 1e6, dt, oracle.num_threads()
+
+
+def bf16_storage_error(torch, P, sc, osc, cam, ref):
+    """Error of BF16 record storage against the FP64 oracle on the FP32
+    records, per output: the 1080p frame the CPU baseline rendered, and a
+    seeded sample of the LiDAR sweep (range, intensity)."""
+    import oracle
+    g16 = P.Scene(sc, dtype="bf16")
+    res = {}
+
+    def stats(a, b):
+        e = np.abs(np.asarray(a, np.float64) - b).ravel()
+        return dict(max=float(e.max()), mean=float(e.mean()),
+                    p999=float(np.quantile(e, 0.999)))
+
+    idx = ref["idx"]
+    o = g16.render(cam, outputs=("rgb", "depth", "opacity"))
+    torch.cuda.synchronize()
+    for k in ("rgb", "depth", "opacity"):
+        res[f"camera_{k}"] = stats(o[k].cpu().numpy()[idx], ref[k])
+    lid = driving_lidar()
+    li = synth.sample_ray_indices(lid["width"] * lid["height"], 65536, 98)
+    rl = oracle.render(osc, lid, idx=li, want_intensity=True)
+    ol = g16.render(lid, outputs=("depth", "opacity", "intensity"), want_intensity=True)
+    torch.cuda.synchronize()
+    for k, name in (("depth", "range"), ("opacity", "opacity"), ("intensity", "intensity")):
+        res[f"lidar_{name}"] = stats(ol[k].cpu().numpy()[li], rl[k])
+    g16.check()
+    g16.close()
+    return dict(note="BF16 records (GPU) vs the FP64 oracle on the FP32 records; absolute "
+                     "errors (depth / range in metres); the tolerance for arithmetic parity "
+                     "(FP32 records, or the oracle on dequantised records) is 1e-4 / 1e-3 m",
+                camera_rays=int(len(idx)), lidar_rays=int(len(li)), **res)
 
 
 def run_reference(args):
@@ -456,7 +527,9 @@ def run_reference(args):
     cam = driving_camera()
     R = cam["width"] * cam["height"]
     rate, _, cores = oracle_rate(osc, cam, 8192, 100)
-    budget_s = 90.0
+    budget_s = 150.0
+    # whole 1080p frames per step when the run fits the time budget, else an
+    # equal seeded sample of each frame's rays
     per_step = int(max(1024, min(R, rate * 1e6 * budget_s / max(1, args.steps + args.warmup))))
     for w in range(args.warmup):
         oracle_rate(osc, cam, per_step, 200 + w)
@@ -466,13 +539,15 @@ def run_reference(args):
         times.append(dt)
     tot = sum(times)
     value = per_step * args.steps / tot / 1e6
+    what = "the whole 1080p frame per step" if per_step == R else \
+        f"{per_step} seeded rays of the 1080p frame per step"
     line = dict(metric=METRIC, value=value, unit="Mrays/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=tot / args.steps * 1e3, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 impl="reference",
-                config=dict(workload=WORKLOAD, sample=f"{per_step} seeded rays of the frame per step"),
+                config=dict(workload=WORKLOAD, sample=what),
                 cpu_baseline=dict(value=value, unit="Mrays/s", cores=cores, kind="oracle",
-                                  sample=f"{per_step} seeded rays of the 1080p frame per step"),
+                                  sample=what),
                 e2e=dict(value=value, unit="Mrays/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
 
@@ -486,7 +561,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="salf", choices=["salf", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--workload", default="camera", choices=["camera", "lidar", "fisheye", "raster"],
                     help="sensor of the headline line (default: the 1080p camera by ray "
                          "casting; raster: the same camera by tile rasterisation)")
@@ -558,12 +633,23 @@ def main():
     peak, peak_kind = hbm_peak()
     achieved = bytes_alg / (avg * 1e-3) / 1e9
     traffic = None
+    inst = None
     try:
         ent = json.load(open(TRAFFIC_FILE)).get(args.workload, {})
         if ent.get("kernel_hash") == kernel_hash(args.workload):
             traffic = ent.get("dram_bytes_per_launch")
+            inst = ent.get("warp_inst_per_launch")
     except Exception:
         pass
+    # issue fraction: warp instructions of the launch (ncu smsp__inst_executed.sum)
+    # over the issue slots of its duration (4 schedulers per SM, one
+    # instruction per cycle each, at the median SM clock seen in the run)
+    issue_frac = None
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    if inst and clocks.get("sm_mhz"):
+        issue_frac = inst / (n_sm * 4 * clocks["sm_mhz"] * 1e6 * avg * 1e-3)
+    from paper_2507_18713_gb300 import _lib as _L
+    param_bytes = int(_L.load().salf_launch_param_bytes())
 
     # end to end through the C ABI with host output buffers (pinned)
     host = {k: torch.empty((R, 3) if k == "rgb" else (R,), dtype=torch.float32, pin_memory=True)
@@ -595,16 +681,19 @@ def main():
                             parallelism=f"replicas x{world}", fps=1e3 / avg,
                             visits_per_ray=nvis / R, t_min=1e-4),
                 roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s",
-                              frac=achieved / peak, traffic=traffic,
+                              frac=achieved / peak, traffic=traffic, issue_frac=issue_frac,
                               peak_source=f"{peak_kind} hbm_gbs",
                               bytes_per_launch=bytes_alg,
                               kernel="k_raster<F32,EXP> (whole pipeline timed)" if raster
                               else "k_forward<F32,EXP>",
                               note="bytes = visits x record scalars read + outputs per ray; "
                                    "visits counted by the kernel"),
-                e2e=dict(value=e2e_value, unit="Mrays/s", h2d_bytes_per_step=0,
+                e2e=dict(value=e2e_value, unit="Mrays/s", h2d_bytes_per_step=param_bytes,
                          d2h_bytes_per_step=R * 4 * (len(outs) + 2 * ("rgb" in outs)),
-                         how=e2e_how),
+                         how=e2e_how,
+                         h2d_note="the launch's kernel parameters (sensor and request "
+                                  "descriptor): rays are generated on the device and the scene "
+                                  "is resident"),
                 gpu_launches=args.steps * launches_per_step, clocks=clocks)
 
     if not args.no_extras and rank == 0:
@@ -717,7 +806,7 @@ def main():
         extra("actors", actors_section)
         del g
         torch.cuda.empty_cache()
-        extra("train_step", lambda: bench_backward(torch, P, args.steps, args.warmup, flush))
+        extra("train_step", lambda: bench_backward(torch, P, args.steps, args.warmup, flush, peak))
         torch.cuda.empty_cache()
         extra("refine", lambda: bench_refine(torch, P, flush))
         torch.cuda.empty_cache()
@@ -728,11 +817,18 @@ def main():
             import oracle
             oracle.build()
             osc = oracle.OracleScene(sc)
-            n_s = 131072
-            rate, dt, cores = oracle_rate(osc, cam, n_s, 99)
+            n_s = R if args.workload in ("camera", "raster") else 131072
+            ref = {}
+            rate, dt, cores = oracle_rate(osc, cam, n_s, 99, outputs=ref)
             line["cpu_baseline"] = dict(value=rate, unit="Mrays/s", cores=cores, kind="oracle",
-                                        sample=f"{n_s} seeded rays of the 1080p frame "
-                                        f"({dt:.1f} s wall)")
+                                        sample=(f"the whole {cam['width']}x{cam['height']} frame"
+                                                if n_s == R else f"{n_s} seeded rays of the frame")
+                                        + f" ({dt:.1f} s wall)")
+            if not args.no_extras and args.workload in ("camera", "raster"):
+                try:
+                    line["bf16_error"] = bf16_storage_error(torch, P, sc, osc, cam, ref)
+                except Exception as e:
+                    line["bf16_error"] = {"error": f"{type(e).__name__}: {e}"}
         except Exception as e:  # the baseline is reported, never required
             line["cpu_baseline"] = dict(value=None, unit="Mrays/s", cores=None, kind="oracle",
                                         sample=f"failed: {e}")

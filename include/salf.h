@@ -246,6 +246,21 @@ salf_status salf_scene_update_params(salf_scene* scene, const float* params,
                                      int32_t params_on_device, void* stream);
 
 /*
+ * Device views of a scene's learnable state (Sec. III-A records), for
+ * wrapping as tensors.  *dev_params (if dev_params is not NULL): the scene's
+ * records, n x 32 in its storage dtype (FP32 or BF16) and in its internal
+ * voxel order (salf_scene_info.dev_order maps internal -> input index);
+ * library-owned, valid until salf_scene_destroy, replaced in place by
+ * salf_scene_update_params.  *dev_grads (if dev_grads is not NULL): the
+ * scene's own FP32 gradient buffer, n x 32 in input order, 16-byte aligned,
+ * created and zeroed by the first call that asks for it (synchronous
+ * cudaMalloc + cudaMemset), freed by salf_scene_destroy; salf_render_backward
+ * with d_params = NULL accumulates into it, and the caller zeroes it between
+ * steps.  Errors: INVALID (null scene), OOM, CUDA.
+ */
+salf_status salf_scene_params(salf_scene* scene, void** dev_params, void** dev_grads);
+
+/*
  * Render all rays of `sensor` (Eq. 1-6 along the voxels each ray crosses).
  * Errors: INVALID (sizes, kind, no output requested), CUDA, DEVICE.
  */
@@ -288,9 +303,13 @@ salf_status salf_render_rays_host_noalloc(salf_scene* scene, const salf_sensor* 
  * d_opacity, d_intensity, d_raydrop (R each; NULL = zero) are dL/d(outputs);
  * with d_raydrop, `raydrop` is the forward's raydrop output (R; its composited
  * part raydrop - T_end enters the suffix sums), else it may be NULL.  d_params
- * (n x 32 FP32, input order, device memory) is ACCUMULATED (+=) with dL/d
- * (record scalars); scalars a field mode does not use receive no gradient.
- * All pointers are device memory.  Asynchronous on `stream`.
+ * (n x 32 FP32, input order, device memory, 16-byte aligned; NULL = the
+ * scene's own gradient buffer, see salf_scene_params) is ACCUMULATED (+=)
+ * with dL/d(record scalars); scalars a field mode does not use receive no
+ * gradient.  All pointers are device memory.  Asynchronous on `stream`.
+ * The only forward outputs the adjoint reads are the per-ray totals in
+ * `saved` (and the raydrop output with d_raydrop): transmittances and every
+ * per-voxel quantity are recomputed by walking the rays again.
  */
 salf_status salf_render_backward(salf_scene* scene, const salf_sensor* sensor,
                                  const salf_render_opts* opts, const float* saved,
@@ -476,17 +495,28 @@ salf_status salf_scene_check(salf_scene* scene);
  * Serving: a host scheduler thread batches requests from many sensors over
  * one resident scene.  mem_budget_bytes bounds the device memory of in-flight
  * requests (outputs); a request waits until its outputs fit (admission by
- * memory).  Admitted requests are packed into batched launches on n_streams
- * streams, so requests that arrive while others run start without waiting
- * for them to finish.  Each request's outputs are identical to a lone
- * salf_render_rays call (rays are independent; no cross-ray reductions).
+ * memory).  Whenever one of the n_streams streams is idle, the oldest waiting
+ * request opens a batch, and waiting requests of the same kernel class join
+ * it in arrival order (up to 24 per launch): pinhole cameras and explicit
+ * rays; fisheye cameras and panoramas; spinning LiDARs (span-parallel rays).
+ * Batches of different classes run side by side on different streams, so
+ * requests that arrive while others run start without waiting for them to
+ * finish.  Each request's outputs are identical to a lone salf_render_rays
+ * call (rays are independent; no cross-ray reductions).
+ * Statistics: p50 / p99 / max latency (submit -> completion) over the last
+ * 65,536 completions; launches, requests launched (their ratio is the mean
+ * batch size), the largest batch, and launches that mixed sensor kinds.
  */
 typedef struct {
   int64_t submitted, completed, rejected;
   int64_t launches;
   int64_t rays;
-  double p50_ms, p99_ms, max_ms;  /* submit -> completion, completed requests */
+  double p50_ms, p99_ms, max_ms;  /* submit -> completion, recent completions */
   int64_t peak_bytes;
+  int64_t requests_launched;      /* sum over launches of the requests each carried */
+  int64_t max_batch;              /* most requests one launch carried */
+  int64_t mixed_launches;         /* launches carrying more than one sensor kind */
+  int64_t latency_window;         /* completions the percentiles are taken over */
 } salf_serve_stats;
 
 salf_status salf_serve_create(salf_scene* scene, size_t mem_budget_bytes, int32_t n_streams,
@@ -505,8 +535,18 @@ salf_status salf_serve_poll(salf_server* srv, uint64_t ticket, int32_t timeout_m
                             salf_outputs* result, int32_t* done);
 salf_status salf_serve_release(salf_server* srv, uint64_t ticket);
 salf_status salf_serve_get_stats(salf_server* srv, salf_serve_stats* stats);
+/* hold != 0: admit nothing (submitted requests queue); hold = 0: resume.
+ * Requests submitted under a hold start together when it is lifted, e.g. all
+ * sensors of one time step, so that they share launches. */
+salf_status salf_serve_hold(salf_server* srv, int32_t hold);
 /* Stops accepting requests, waits for in-flight work, frees everything. */
 void salf_serve_destroy(salf_server* srv);
+
+/* Bytes of kernel parameters that one render launch carries from the host:
+ * the batch descriptor (scene view and request descriptors, prepared in FP64
+ * on the host).  Rays are generated on the device and the scene is resident,
+ * so this is all a device-output render sends to the GPU. */
+size_t salf_launch_param_bytes(void);
 
 /* Thread-local message of the last failing call on this thread. */
 const char* salf_last_error(void);

@@ -62,7 +62,9 @@ class SceneInfo(C.Structure):
 class ServeStats(C.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("rejected", c_int64),
                 ("launches", c_int64), ("rays", c_int64), ("p50_ms", c_double),
-                ("p99_ms", c_double), ("max_ms", c_double), ("peak_bytes", c_int64)]
+                ("p99_ms", c_double), ("max_ms", c_double), ("peak_bytes", c_int64),
+                ("requests_launched", c_int64), ("max_batch", c_int64),
+                ("mixed_launches", c_int64), ("latency_window", c_int64)]
 
 
 class Actor(C.Structure):
@@ -96,6 +98,7 @@ SIGNATURES = {
     "salf_scene_destroy": ([c_void_p], None),
     "salf_scene_get_info": ([c_void_p, C.POINTER(SceneInfo)], c_int32),
     "salf_scene_update_params": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
+    "salf_scene_params": ([c_void_p, C.POINTER(c_void_p), C.POINTER(c_void_p)], c_int32),
     "salf_render_rays": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts), C.POINTER(Outputs),
                           c_void_p], c_int32),
     "salf_render_rays_actors": ([c_void_p, C.POINTER(Actor), c_int32, C.POINTER(Sensor),
@@ -123,7 +126,9 @@ SIGNATURES = {
                         c_int32),
     "salf_serve_release": ([c_void_p, C.c_uint64], c_int32),
     "salf_serve_get_stats": ([c_void_p, C.POINTER(ServeStats)], c_int32),
+    "salf_serve_hold": ([c_void_p, c_int32], c_int32),
     "salf_serve_destroy": ([c_void_p], None),
+    "salf_launch_param_bytes": ([], C.c_size_t),
     "salf_last_error": ([], C.c_char_p),
 }
 

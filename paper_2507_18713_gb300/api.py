@@ -173,6 +173,22 @@ class Scene:
     def check(self):
         L.check(L.load().salf_scene_check(self._h), "salf_scene_check")
 
+    def grads_view(self) -> torch.Tensor:
+        """salf_scene_params: zero-copy (n, 32) float32 CUDA view of the scene's
+        own gradient buffer (input order), which backward(d_params="scene")
+        accumulates into; library-owned, valid while the scene lives."""
+        g = C.c_void_p()
+        L.check(L.load().salf_scene_params(self._h, None, C.byref(g)), "salf_scene_params")
+        return device_view(g.value, (self.n, 32), "<f4")
+
+    def params_view(self) -> torch.Tensor:
+        """salf_scene_params: zero-copy (n, 32) view of the scene's records in
+        its storage dtype and internal voxel order (info()["dev_order"] maps
+        internal -> input index)."""
+        p = C.c_void_p()
+        L.check(L.load().salf_scene_params(self._h, C.byref(p), None), "salf_scene_params")
+        return device_view(p.value, (self.n, 32), "<f4" if self.dtype == "f32" else "<u2")
+
     def update_params(self, params, stream=None):
         """salf_scene_update_params: params (n, 32) float32, input order."""
         lib = L.load()
@@ -422,10 +438,14 @@ class Scene:
                  d_intensity=None, d_params=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
                  want_intensity=False, stream=None, raydrop=None, d_raydrop=None):
         """salf_render_backward: returns d_params (n, 32) float32 (accumulated
-        into the given tensor if any).  With d_raydrop, `raydrop` is the
+        into the given tensor if any; the string "scene" accumulates into the
+        scene's own buffer, grads_view()).  With d_raydrop, `raydrop` is the
         forward's raydrop output."""
         dev = torch.device("cuda", self.ctx.device)
-        if d_params is None:
+        own = isinstance(d_params, str) and d_params == "scene"
+        if own:
+            d_params = self.grads_view()
+        elif d_params is None:
             d_params = torch.zeros((self.n, 32), dtype=torch.float32, device=dev)
 
         def ptr(t):
@@ -437,8 +457,8 @@ class Scene:
         op = opts_struct(t_min, background, want_intensity, 0)
         L.check(L.load().salf_render_backward(
             self._h, C.byref(s), C.byref(op), saved.data_ptr(), ptr(d_rgb), ptr(d_depth),
-            ptr(d_opacity), ptr(d_intensity), ptr(raydrop), ptr(d_raydrop), d_params.data_ptr(),
-            _stream_ptr(stream)),
+            ptr(d_opacity), ptr(d_intensity), ptr(raydrop), ptr(d_raydrop),
+            None if own else d_params.data_ptr(), _stream_ptr(stream)),
             "salf_render_backward")
         return d_params
 
@@ -462,10 +482,14 @@ class RenderFn(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_opacity):
+        # accumulate into the scene's own gradient buffer (salf_scene_params),
+        # then hand autograd a copy it may keep
         (saved,) = ctx.saved_tensors
-        d = ctx.scene.backward(ctx.sensor, saved, d_rgb=g_rgb, d_depth=g_depth,
-                               d_opacity=g_opacity, t_min=ctx.t_min, background=ctx.background)
-        return d, None, None, None, None
+        own = ctx.scene.grads_view()
+        own.zero_()
+        ctx.scene.backward(ctx.sensor, saved, d_rgb=g_rgb, d_depth=g_depth, d_opacity=g_opacity,
+                           t_min=ctx.t_min, background=ctx.background, d_params="scene")
+        return own.clone(), None, None, None, None
 
 
 class Server:
@@ -522,6 +546,11 @@ class Server:
     def release(self, ticket: int):
         L.check(L.load().salf_serve_release(self._h, C.c_uint64(ticket)), "salf_serve_release")
         self._sensors.pop(ticket, None)
+
+    def hold(self, on: bool = True):
+        """salf_serve_hold: while held, submitted requests wait; releasing the
+        hold starts them together."""
+        L.check(L.load().salf_serve_hold(self._h, int(bool(on))), "salf_serve_hold")
 
     def stats(self) -> dict:
         s = L.ServeStats()

@@ -23,6 +23,8 @@ salf_status salf_cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" const char* salf_last_error(void) { return g_err.c_str(); }
 
+extern "C" size_t salf_launch_param_bytes(void) { return sizeof(LaunchParams); }
+
 extern "C" salf_status salf_create(int32_t device, salf_ctx** out) {
   if (!out) {
     g_err = "salf_create: null out";
@@ -59,6 +61,7 @@ extern "C" void salf_scene_destroy(salf_scene* s) {
   cudaDeviceSynchronize();
   for (void* p : s->allocations) cudaFree(p);
   if (s->staging) cudaFree(s->staging);
+  if (s->grads) cudaFree(s->grads);
   if (s->raster_vox) cudaFree(s->raster_vox);
   if (s->raster_pairs) cudaFree(s->raster_pairs);
   if (s->raster_count_host) cudaFreeHost(s->raster_count_host);
@@ -89,6 +92,34 @@ extern "C" salf_status salf_scene_get_info(const salf_scene* s, salf_scene_info*
   info->device_bytes = s->device_bytes;
   info->dev_params = s->dev.params;
   info->dev_order = s->dev.order;
+  return SALF_OK;
+}
+
+extern "C" salf_status salf_scene_params(salf_scene* s, void** dev_params, void** dev_grads) {
+  if (!s) {
+    g_err = "salf_scene_params: null scene";
+    return SALF_ERR_INVALID;
+  }
+  if (dev_params) *dev_params = const_cast<void*>(s->dev.params);
+  if (!dev_grads) return SALF_OK;
+  std::lock_guard<std::mutex> lk(s->grads_mu);
+  if (!s->grads) {
+    cudaError_t e;
+    if ((e = cudaSetDevice(s->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+    const size_t bytes = (size_t)(s->n > 0 ? s->n : 1) * SALF_RECORD_SCALARS * sizeof(float);
+    float* g = nullptr;
+    if ((e = cudaMalloc(&g, bytes)) != cudaSuccess) return salf_cuda_fail(e, "cudaMalloc(grads)");
+    if ((e = cudaMemset(g, 0, bytes)) != cudaSuccess) {
+      cudaFree(g);
+      return salf_cuda_fail(e, "cudaMemset(grads)");
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+      cudaFree(g);
+      return salf_cuda_fail(e, "cudaMemset(grads)");
+    }
+    s->grads = g;
+  }
+  *dev_grads = s->grads;
   return SALF_OK;
 }
 
@@ -893,9 +924,18 @@ extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* s
                                             const float* d_opacity, const float* d_intensity,
                                             const float* raydrop, const float* d_raydrop,
                                             float* d_params, void* stream) {
-  if (!sc || !sen || !saved || !d_params) {
+  if (!sc || !sen || !saved) {
     g_err = "salf_render_backward: null argument";
     return SALF_ERR_INVALID;
+  }
+  if (!d_params) {  // the scene's own gradient buffer
+    std::lock_guard<std::mutex> lk(sc->grads_mu);
+    d_params = sc->grads;
+    if (!d_params) {
+      g_err = "salf_render_backward: d_params is NULL and salf_scene_params has not created the "
+              "scene's gradient buffer";
+      return SALF_ERR_INVALID;
+    }
   }
   if (d_raydrop && !raydrop) {
     g_err = "salf_render_backward: d_raydrop needs the forward's raydrop output";

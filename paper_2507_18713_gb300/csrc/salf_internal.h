@@ -190,6 +190,9 @@ struct salf_scene {
   double s0 = 0, sfin = 0;
   int64_t n_cells0 = 0, n_nodes = 0, device_bytes = 0;
   std::vector<void*> allocations;  // every device buffer the scene owns
+  // library-owned FP32 gradient buffer (n x 32, input order; salf_scene_params)
+  std::mutex grads_mu;
+  float* grads = nullptr;
   // staging for host-memory outputs / explicit rays (grown on demand)
   std::mutex staging_mu;
   void* staging = nullptr;

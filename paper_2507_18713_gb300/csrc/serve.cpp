@@ -1,15 +1,19 @@
 // serve.cpp -- continuous-batching render server over one resident scene.
 //
-// A scheduler thread admits queued requests in arrival order as long as their
-// outputs fit in a fixed device arena (admission by memory), packs up to
-// SALF_MAX_BATCH admitted requests into one launch of the forward kernel
-// (each request keeps its own sensor, options and output slice), and issues it
-// on an idle stream.  Requests that arrive while batches run join the next
-// batch as soon as a stream frees up, so work from different requests
-// overlaps on the device.  Completion is signalled by a host function queued
-// behind each batch on its stream.  Rays are independent and the batched
-// launch runs the same per-ray code as salf_render_rays, so a request's
-// outputs do not depend on what it was batched with.
+// A scheduler thread forms batches whenever a stream is idle.  A batch takes
+// the oldest queued request and then, in arrival order, further queued
+// requests of the same kernel class (coherent cameras and explicit rays;
+// divergent cameras -- fisheye, panorama; span-parallel rays -- spinning
+// LiDARs), up to SALF_MAX_BATCH, as long as their outputs fit in a fixed
+// device arena (admission by memory).  Each class has its own kernel shape,
+// so a batch is one launch of the forward kernel (each request keeps its own
+// sensor, options and output slice) and batches of different classes run
+// side by side on different streams.  Requests that arrive while batches run
+// join the next batch as soon as a stream frees up, so work from different
+// requests overlaps on the device.  Completion is signalled by a host
+// function queued behind each batch on its stream.  Rays are independent and
+// the batched launch runs the same per-ray code as salf_render_rays, so a
+// request's outputs do not depend on what it was batched with.
 //
 // Host-side fault injection for tests (environment variable SALF_SERVE_FAULT):
 //   "launch_fail:N"  the N-th batch (1-based) is not launched and its requests
@@ -39,6 +43,7 @@ enum class St { Queued, Running, Done, Failed };
 
 struct Request {
   uint64_t ticket = 0;
+  int cls = 0;  // kernel class (batch_class)
   salf_sensor sensor{};
   salf_render_opts opts{};
   ReqDev rd{};
@@ -97,6 +102,10 @@ struct Arena {
 
 }  // namespace
 
+// Latencies of the most recent completions (a fixed window keeps a long-
+// running server's memory and stats cost bounded).
+constexpr size_t kLatencyWindow = 1 << 16;
+
 struct salf_server {
   salf_scene* scene = nullptr;
   char* arena_base = nullptr;
@@ -107,10 +116,13 @@ struct salf_server {
   std::condition_variable cv_sched, cv_done;
   std::deque<uint64_t> pending;
   std::unordered_map<uint64_t, Request> reqs;
-  std::vector<double> latencies_ms;
+  std::vector<double> latencies_ms;  // ring of the last kLatencyWindow completions
+  size_t lat_next = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
+  bool hold = false;
   int64_t submitted = 0, completed = 0, rejected = 0, launches = 0, rays = 0;
+  int64_t requests_launched = 0, max_batch = 0, mixed_launches = 0;
   int64_t fail_launch_at = -1;
   std::thread th;
 };
@@ -138,8 +150,13 @@ void CUDART_CB on_batch_done(void* p) {
       r.err = b->status;
       r.t_done = now;
       s->completed++;
-      s->latencies_ms.push_back(
-          std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count());
+      const double ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+      if (s->latencies_ms.size() < kLatencyWindow) {
+        s->latencies_ms.push_back(ms);
+      } else {
+        s->latencies_ms[s->lat_next] = ms;
+        s->lat_next = (s->lat_next + 1) % kLatencyWindow;
+      }
     }
     s->stream_busy[b->stream]--;
   }
@@ -149,6 +166,14 @@ void CUDART_CB on_batch_done(void* p) {
 }
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// Kernel class of a prepared request: requests of one class share a forward
+// variant and so a launch (0: pinhole cameras and explicit rays, whole rays;
+// 1: fisheye and panorama, whole rays; 2: span-parallel rays).
+int batch_class(const ReqDev& d) {
+  if (d.seg_shift > 0) return 2;
+  return (d.kind == SALF_PINHOLE || d.kind == SALF_RAYS_EXPLICIT) ? 0 : 1;
+}
 
 // Output layout of one request inside the arena.
 size_t layout(Request& r, char* base) {
@@ -179,18 +204,24 @@ void scheduler(salf_server* s) {
         idle = (int)i;
         break;
       }
-    // admit in arrival order while the head fits
+    // the oldest request opens a batch; queued requests of its kernel class
+    // join it in arrival order while their outputs fit
     std::vector<uint64_t> batch;
-    if (idle >= 0) {
-      while (!s->pending.empty() && batch.size() < SALF_MAX_BATCH) {
-        Request& r = s->reqs[s->pending.front()];
+    if (idle >= 0 && !s->hold && !s->pending.empty()) {
+      const int cls = s->reqs[s->pending.front()].cls;
+      for (auto it = s->pending.begin(); it != s->pending.end() && batch.size() < SALF_MAX_BATCH;) {
+        Request& r = s->reqs[*it];
+        if (r.cls != cls) {
+          ++it;
+          continue;
+        }
         size_t off;
         if (!s->arena.alloc(r.bytes, &off)) break;
         r.offset = off;
         layout(r, s->arena_base + off);
         r.state = St::Running;
         batch.push_back(r.ticket);
-        s->pending.pop_front();
+        it = s->pending.erase(it);
       }
     }
     if (batch.empty()) {
@@ -219,6 +250,13 @@ void scheduler(salf_server* s) {
     P->step_budget = salf_step_budget();
     s->stream_busy[idle]++;
     s->launches++;
+    s->requests_launched += (int64_t)batch.size();
+    s->max_batch = std::max<int64_t>(s->max_batch, (int64_t)batch.size());
+    for (int i = 1; i < P->n_req; ++i)
+      if (P->req[i].kind != P->req[0].kind) {
+        s->mixed_launches++;
+        break;
+      }
     const bool inject = s->fail_launch_at > 0 && s->launches == s->fail_launch_at;
     BatchDone* bd = new BatchDone{s, idle, batch, SALF_OK};
     cudaStream_t st = s->streams[idle];
@@ -306,6 +344,7 @@ extern "C" salf_status salf_serve_submit(salf_server* s, const salf_sensor* sens
   if (st != SALF_OK) return st;
   r.rays = salf_request_rays(&r.sensor);
   r.bytes = layout(r, nullptr);
+  r.cls = batch_class(r.rd);
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) {
     salf_set_error("salf_serve_submit: server is shutting down");
@@ -402,21 +441,41 @@ extern "C" salf_status salf_serve_release(salf_server* s, uint64_t ticket) {
   return SALF_OK;
 }
 
+extern "C" salf_status salf_serve_hold(salf_server* s, int32_t hold) {
+  if (!s) {
+    salf_set_error("salf_serve_hold: null server");
+    return SALF_ERR_INVALID;
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->hold = hold != 0;
+  }
+  s->cv_sched.notify_all();
+  return SALF_OK;
+}
+
 extern "C" salf_status salf_serve_get_stats(salf_server* s, salf_serve_stats* st) {
   if (!s || !st) {
     salf_set_error("salf_serve_get_stats: null argument");
     return SALF_ERR_INVALID;
   }
-  std::lock_guard<std::mutex> lk(s->mu);
-  std::memset(st, 0, sizeof(*st));
-  st->submitted = s->submitted;
-  st->completed = s->completed;
-  st->rejected = s->rejected;
-  st->launches = s->launches;
-  st->rays = s->rays;
-  st->peak_bytes = (int64_t)s->arena.peak;
-  if (!s->latencies_ms.empty()) {
-    std::vector<double> v = s->latencies_ms;
+  std::vector<double> v;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(st, 0, sizeof(*st));
+    st->submitted = s->submitted;
+    st->completed = s->completed;
+    st->rejected = s->rejected;
+    st->launches = s->launches;
+    st->rays = s->rays;
+    st->peak_bytes = (int64_t)s->arena.peak;
+    st->requests_launched = s->requests_launched;
+    st->max_batch = s->max_batch;
+    st->mixed_launches = s->mixed_launches;
+    v = s->latencies_ms;  // percentiles are taken outside the lock
+  }
+  st->latency_window = (int64_t)v.size();
+  if (!v.empty()) {
     std::sort(v.begin(), v.end());
     auto q = [&](double p) {
       const size_t i = (size_t)std::min<double>(v.size() - 1, std::ceil(p * v.size()) - 1);

@@ -17,3 +17,16 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter):
+    try:
+        from tests.parity_util import VISIT_LOG
+    except Exception:
+        return
+    if not VISIT_LOG:
+        return
+    tr = terminalreporter
+    tr.write_sep("-", "visit lists that differ from the oracle's, each explained by the margin")
+    for name, n, bad in VISIT_LOG:
+        tr.write_line(f"{bad:6d} of {n:9d} rays ({100.0 * bad / max(n, 1):.3f}%)  {name}")

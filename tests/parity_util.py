@@ -2,7 +2,13 @@
 
 from __future__ import annotations
 
+import os
+
 import numpy as np
+
+# (test, rays compared, rays whose GPU visit list differs from the oracle's
+# and is explained by the eps margin), printed at the end of the session
+VISIT_LOG: list = []
 
 # Tolerances (FP32 kernels vs the FP64 oracle): colour / opacity / intensity
 # absolute 1e-4, depth / range absolute 1e-3 m.
@@ -126,6 +132,8 @@ def check_visits(oracle, osc, sensor, scene, g_vis, g_cnt, o_vis, o_cnt, idx):
         pos = {v: i for i, v in enumerate(grown)}
         for a, c in zip(gl, gl[1:]):
             assert g_in[pos[a]] <= g_out[pos[c]], (ray_id, gl, grown)
+    VISIT_LOG.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], len(g_cnt),
+                      len(bad)))
     return len(g_cnt), len(bad)
 
 

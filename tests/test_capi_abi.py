@@ -16,8 +16,8 @@ def _declared_functions():
 
 def test_header_declares_the_boundary():
     names = _declared_functions()
-    for required in ("salf_build_scene", "salf_render_rays", "salf_render_backward",
-                     "salf_serve_submit", "salf_serve_poll"):
+    for required in ("salf_build_scene", "salf_scene_params", "salf_render_rays",
+                     "salf_render_backward", "salf_serve_submit", "salf_serve_poll"):
         assert required in names
 
 
@@ -40,6 +40,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(L.RasterStats) == 8 + 8 + 4 + 4 + 4 + 4
     # kind, eta, light_dir[3], min_opacity, offset, t_far
     assert ctypes.sizeof(L.SecondaryOpts) == 4 * 8
+    # counters, 3 doubles, peak bytes, then the batching counters
+    assert ctypes.sizeof(L.ServeStats) == 5 * 8 + 3 * 8 + 8 + 4 * 8
 
 
 def test_binding_marshals_the_new_options():

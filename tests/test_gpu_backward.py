@@ -137,6 +137,29 @@ def test_autograd_function_linear_loss(salf, oracle_lib):
     grad_close(params.grad.cpu().numpy(), do, bnd)
 
 
+def test_scene_params_views(salf):
+    """salf_scene_params: the records view is the scene's storage in internal
+    order (dev_order maps back to the input); the scene-owned gradient buffer
+    receives the same adjoint as a caller buffer."""
+    sc = synth.random_multilevel_scene(seed=8, max_level=2, dims=(5, 4, 3), p_occ=0.8)
+    sen = synth.pinhole(32, 24, 70.0, synth.camera_pose_looking((-1.9, 0.25, 0.9), 0.1))
+    g = salf.Scene(sc)
+    order = salf.device_view(g.info()["dev_order"], (sc.n,), "<i4").cpu().numpy()
+    pv = g.params_view().cpu().numpy()
+    assert np.array_equal(pv, sc.params.astype(np.float32)[order])
+    out = g.render(sen, saved=True, outputs=("rgb",), t_min=0.0)
+    w = torch.from_numpy(np.random.default_rng(2).normal(size=(32 * 24, 3)).astype(np.float32)).cuda()
+    mine = g.backward(sen, out["saved"], d_rgb=w, t_min=0.0)
+    own = g.grads_view()
+    assert float(own.abs().max()) == 0.0  # created zeroed
+    g.backward(sen, out["saved"], d_rgb=w, t_min=0.0, d_params="scene")
+    g.backward(sen, out["saved"], d_rgb=w, t_min=0.0, d_params="scene")  # accumulates
+    torch.cuda.synchronize()
+    g.check()
+    a, b = own.cpu().numpy(), mine.cpu().numpy()
+    assert np.allclose(a, 2 * b, rtol=1e-5, atol=1e-6)
+
+
 def test_training_step_reduces_mse(salf):
     """A few Adam steps through RenderFn lower an image MSE (adjoint sign and
     scale are usable for optimisation)."""

@@ -76,7 +76,47 @@ def test_each_result_equals_lone_render(salf, scene):
         srv.release(t)
     st = srv.stats()
     assert st["completed"] == len(sensors) and st["launches"] >= 1
+    assert st["requests_launched"] == len(sensors) and st["latency_window"] == len(sensors)
     assert st["p99_ms"] >= st["p50_ms"] > 0
+    srv.close()
+
+
+def test_held_requests_share_launches_and_equal_lone_renders(salf, scene):
+    """Requests submitted under a hold start together: requests of one kernel
+    class share a launch (two pinholes and explicit rays in one, a fisheye and
+    a panorama in another, two LiDARs in a third), so launches carry several
+    sensor kinds, and every result equals its lone render bit for bit."""
+    rng = np.random.default_rng(3)
+    cam = lambda w, h: synth.pinhole(w, h, 70.0, synth.camera_pose_looking((-2.1, 0.5, 1.05), 0.2))
+    o = np.array([-2.0, 0.6, 1.0])
+    d = rng.normal(size=(500, 3)) * 0.3 + np.array([1.0, 0.0, 0.0])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.concatenate([np.tile(o, (500, 1)), d, np.zeros((500, 2))], axis=1)
+    sensors = [cam(64, 48), synth.fisheye(64, 48, 190.0, synth.camera_pose_looking(
+                   (-2.0, 0.7, 1.1), 0.3)),
+               synth.lidar(16, 256, synth.lidar_pose((0.3, 0.5, 1.0), 0.1),
+                           synth.lidar_pose((0.6, 0.6, 1.0), 0.2), t0=0, t1=0.1),
+               synth.explicit_rays(rays), cam(40, 30),
+               synth.panorama(128, 32, synth.camera_pose_looking((-1.9, 0.6, 1.0), 0.0)),
+               synth.lidar(8, 128, synth.lidar_pose((0.4, 0.5, 1.0), 0.3),
+                           synth.lidar_pose((0.5, 0.6, 1.0), 0.3), t0=0, t1=0.1)]
+    srv = salf.Server(scene, mem_budget_bytes=64 << 20, n_streams=2)
+    srv.hold(True)
+    tickets = [srv.submit(s, want_intensity=s["kind"] == "lidar") for s in sensors]
+    time.sleep(0.05)
+    assert srv.stats()["launches"] == 0   # nothing starts under the hold
+    srv.hold(False)
+    for s, t in zip(sensors, tickets):
+        res = srv.fetch(t, timeout_ms=20000)
+        lone = _lone(scene, s)
+        keys = ("depth", "opacity", "valid") + (("intensity",) if s["kind"] == "lidar" else ("rgb",))
+        for k in keys:
+            assert torch.equal(res[k], lone[k]), (s["kind"], k)
+        srv.release(t)
+    st = srv.stats()
+    print(st)
+    assert st["launches"] == 3 and st["requests_launched"] == len(sensors)
+    assert st["mixed_launches"] == 2 and st["max_batch"] == 3
     srv.close()
 
 
