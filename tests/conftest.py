@@ -28,5 +28,11 @@ def pytest_terminal_summary(terminalreporter):
         return
     tr = terminalreporter
     tr.write_sep("-", "visit lists that differ from the oracle's, each explained by the margin")
-    for name, n, bad in VISIT_LOG:
-        tr.write_line(f"{bad:6d} of {n:9d} rays ({100.0 * bad / max(n, 1):.3f}%)  {name}")
+    lines = [f"{bad:6d} of {n:9d} rays ({100.0 * bad / max(n, 1):.3f}%)  {name}"
+             for name, n, bad in VISIT_LOG]
+    for ln in lines:
+        tr.write_line(ln)
+    path = os.environ.get("SALF_VISIT_LOG")
+    if path:
+        with open(path, "w") as f:
+            f.write("\n".join(lines) + "\n")

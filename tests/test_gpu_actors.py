@@ -73,7 +73,7 @@ def actor_sensitivity(oracle, osc, oactors, sensor, idx, kappa=KAPPA, **kw):
 
 
 def _parity(salf, oracle_lib, scene, actor_scenes, tracks, sensor, dtype="f32", idx=None,
-            want_intensity=True, max_bad_visits=0.01):
+            want_intensity=True, max_bad_visits=0.001):
     g = salf.Scene(scene, dtype=dtype)
     osc = oracle_lib.OracleScene(scene)
     gact, oact = [], []
@@ -101,6 +101,10 @@ def _parity(salf, oracle_lib, scene, actor_scenes, tracks, sensor, dtype="f32", 
     n = len(cnt)
     actor_hits = int((ov["visits"] >= base).any(axis=1).sum())
     g.check()
+    import os
+    from tests.parity_util import VISIT_LOG
+    VISIT_LOG.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0] + " (actors)", n,
+                      bad))
     assert bad <= max(2, int(max_bad_visits * n)), (bad, n)
     return dict(errs=errs, bad_visits=bad, rays=n, rays_hitting_actors=actor_hits)
 

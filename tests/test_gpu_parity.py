@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.parity_util import (TOL_C, TOL_D, check_visits, compare_outputs, gpu_render,
+from tests.parity_util import (TOL_C, TOL_D, check_visits, visit_cap, compare_outputs, gpu_render,
                                oracle_sensitivity, to_np)
 
 pytestmark = pytest.mark.gpu
@@ -57,7 +57,7 @@ def test_tiny_scene_pinhole(salf, oracle_lib):
     sc = synth.tiny_scene(seed=1)
     res = _full(salf, oracle_lib, sc, c1_camera())
     n, bad = res["visits"]
-    assert bad <= max(3, n // 100), res
+    assert bad <= visit_cap(n), res
     res0 = _full(salf, oracle_lib, sc, c1_camera(), t_min=0.0, visits=False)
     assert res0["errs"]["max_c"] <= TOL_C
 
@@ -78,7 +78,7 @@ def test_multilevel_all_sensors(salf, oracle_lib, seed, K):
     for sen in sensors:
         res = _full(salf, oracle_lib, sc, sen, want_intensity=True, background=(0.1, 0.2, 0.3))
         n, bad = res["visits"]
-        assert bad <= max(2, n // 100), (sen["kind"], res)
+        assert bad <= visit_cap(n), (sen["kind"], res)
 
 
 def test_explicit_rays_edge_cases(salf, oracle_lib):
@@ -100,14 +100,14 @@ def test_explicit_rays_edge_cases(salf, oracle_lib):
     sen = synth.explicit_rays(rays)
     res = _full(salf, oracle_lib, sc, sen, want_intensity=True)
     n, bad = res["visits"]
-    assert bad <= max(3, n // 50), res
+    assert bad <= visit_cap(n), res
 
 
 def test_sdf_mode(salf, oracle_lib):
     sc = synth.random_multilevel_scene(seed=4, max_level=2, dims=(6, 5, 4), p_occ=0.7, mode="sdf")
     sen = synth.pinhole(64, 48, 75.0, synth.camera_pose_looking((-2.2, 0.6, 1.1), 0.15))
     res = _full(salf, oracle_lib, sc, sen, want_intensity=True)
-    assert res["visits"][1] <= 30
+    assert res["visits"][1] <= visit_cap(res["visits"][0]), res
 
 
 def test_bf16_records(salf, oracle_lib):
@@ -146,11 +146,11 @@ def test_deep_octree_all_levels(salf, oracle_lib):
     sen = synth.explicit_rays(np.array(rays))
     res = _full(salf, oracle_lib, sc, sen, t_min=0.0, brute=True)
     n, bad = res["visits"]
-    assert bad <= max(3, n // 50), res
+    assert bad <= visit_cap(n), res
     assert res["mean_visits"] > 3
     cam = synth.pinhole(96, 72, 80.0, synth.camera_pose_looking((-1.5, 0.9, 1.1), 0.1))
     res = _full(salf, oracle_lib, sc, cam, brute=True)
-    assert res["visits"][1] <= max(3, res["visits"][0] // 100)
+    assert res["visits"][1] <= visit_cap(res["visits"][0]), res
 
 
 def test_size_limits_rejected(salf):
@@ -333,7 +333,7 @@ def test_driving_1080p_pinhole_sampled(oracle_lib, driving):
     res = _sampled(oracle_lib, driving, cam, 65536, 11)
     print("1080p pinhole:", res)
     n, bad = res["visits"]
-    assert bad <= n // 100
+    assert bad <= visit_cap(n)
 
 
 def test_driving_lidar_sampled(oracle_lib, driving):
@@ -342,7 +342,7 @@ def test_driving_lidar_sampled(oracle_lib, driving):
     res = _sampled(oracle_lib, driving, lid, 65536, 12, want_intensity=True)
     print("LiDAR 128x2048:", res)
     n, bad = res["visits"]
-    assert bad <= n // 100
+    assert bad <= visit_cap(n)
 
 
 def test_driving_fisheye_sampled(oracle_lib, driving):
@@ -350,7 +350,7 @@ def test_driving_fisheye_sampled(oracle_lib, driving):
     res = _sampled(oracle_lib, driving, fe, 32768, 13, visits=True)
     print("fisheye 1080p:", res)
     n, bad = res["visits"]
-    assert bad <= n // 100
+    assert bad <= visit_cap(n)
 
 
 def test_driving_identical_rays(oracle_lib, driving):
@@ -373,7 +373,7 @@ def test_driving_identical_rays(oracle_lib, driving):
     n, bad = check_visits(oracle_lib, osc, sen, sc, gv["visits"], gv["visit_count"], ov["visits"],
                           ov["n_visits"], None)
     print("identical rays:", res, "visit lists explained by eps:", bad, "of", n)
-    assert bad <= n // 200
+    assert bad <= visit_cap(n)
 
 
 @pytest.mark.parametrize("kind", ["pinhole", "fisheye", "pano", "lidar", "rolling"])

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.parity_util import (TOL_C, TOL_D, check_visits, compare_outputs, gpu_render,
+from tests.parity_util import (TOL_C, TOL_D, check_visits, visit_cap, compare_outputs, gpu_render,
                                oracle_sensitivity, to_np)
 
 pytestmark = pytest.mark.gpu
@@ -86,7 +86,7 @@ def test_tiny_scene(salf, oracle_lib):
     print(res)
     assert res["equal_frac"] >= 0.999 and res["max_vs_ray"] <= TOL_C, res
     n, bad = res["visits"]
-    assert bad <= max(3, n // 100), res
+    assert bad <= visit_cap(n), res
     assert res["stats"]["pairs"] > 0 and res["stats"]["visible_voxels"] > 0
 
 
@@ -109,7 +109,7 @@ def test_multilevel_cameras(salf, oracle_lib, seed, K):
         res = _parity(salf, oracle_lib, sc, sen, want_intensity=True, background=(0.1, 0.2, 0.3))
         assert res["max_vs_ray"] <= TOL_C, (sen["width"], res)
         n, bad = res["visits"]
-        assert bad <= max(2, n // 100), (sen["width"], res)
+        assert bad <= visit_cap(n), (sen["width"], res)
 
 
 def test_sdf_and_bf16(salf, oracle_lib):
@@ -200,5 +200,5 @@ def test_driving_frame(oracle_lib, driving, w, h, yaw):
     ov = oracle_lib.render(osc, cam, idx=idx, t_min=0.0, visits_cap=cap)
     n, bad = check_visits(oracle_lib, osc, cam, sc, gv["visits"], gv["visit_count"], ov["visits"],
                           ov["n_visits"], idx)
-    assert bad <= n // 100
+    assert bad <= visit_cap(n)
     g.check()
