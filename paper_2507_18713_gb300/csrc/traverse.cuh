@@ -9,9 +9,12 @@
 
 #include "salf_internal.h"
 
-// Traversal tuning switch (compile-time).
+// Traversal tuning switches (compile-time).
 #ifndef SALF_COL_MAX_LS
 #define SALF_COL_MAX_LS 0  // > 0: try the column skip only below this pyramid leaf size
+#endif
+#ifndef SALF_COL_EARLY
+#define SALF_COL_EARLY 1  // 1: load the column mask beside the pyramid word; 0: only for empty cells
 #endif
 
 namespace salf {
@@ -393,7 +396,9 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
   for (int it = 0; it < budget && w.alive; ++it) {
     // the column mask depends only on the cell: issue its load with the pyramid's
     const int cl = w.cl;
+#if SALF_COL_EARLY
     const uint4 cmask = col_mask(S, w, cl);
+#endif
     int ls;
     const int vox = find_leaf(S, w.c[0], w.c[1], w.c[2], &ls);
     const int E = 1 << ls;
@@ -437,6 +442,9 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
       if (ls <= SALF_COL_MAX_LS + S.K)
 #endif
       {
+#if !SALF_COL_EARLY
+        const uint4 cmask = col_mask(S, w, cl);
+#endif
         ok = col_skip(S, w, cl, cmask, &cte, clo, chi, &cax);
         w.cl = ok ? min(cl + 1, S.CL - 1) : max(cl - 1, 0);
       }
