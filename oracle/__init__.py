@@ -19,6 +19,7 @@ from .oracle import (  # noqa: F401
     secondary_rays,
     voxel_at,
     backward,
+    backward_actors,
     conditioned,
     gen_rays,
     trace,

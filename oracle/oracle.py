@@ -100,6 +100,9 @@ def _load():
             lib.orc_backward_bound.argtypes = lib.orc_backward.argtypes
             lib.orc_scene_set_record.argtypes = [vp, i64, vp]
             lib.orc_conditioned.argtypes = [vp, C.POINTER(_Sensor), vp, i64, dp, dp, vp]
+            lib.orc_backward_actors.argtypes = [vp, vp, i32, C.POINTER(_Sensor), C.POINTER(_Opts),
+                                                vp, i64, vp, vp, vp, vp, vp, vp]
+            lib.orc_backward_actors_bound.argtypes = lib.orc_backward_actors.argtypes
             lib.orc_num_threads.restype = C.c_int
             lib.orc_subdivide_record.argtypes = [vp, i32, vp]
             lib.orc_render_actors.argtypes = [vp, vp, i32, C.POINTER(_Sensor), C.POINTER(_Opts),
@@ -392,6 +395,45 @@ def render_actors(oscene, actors, sensor, idx=None, t_min=1e-4, background=(0.0,
     del keep
     res["valid"] = res["valid"].astype(bool)
     return res
+
+
+def backward_actors(oscene, actors, sensor, g_rgb=None, g_depth=None, g_opacity=None,
+                    g_intensity=None, idx=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                    want_intensity=False, brute_force=False, bound=False):
+    """Adjoint of render_actors: (static gradient (n, 32), [actor k's gradient
+    (n_k, 32)]) of sum(g . outputs) w.r.t. every record scalar.  With
+    bound=True, also the FP32 rounding bounds, in the same shapes."""
+    lib = _load()
+    s, keep = _sensor(sensor)
+    idx, m = _idx(sensor, idx)
+    arr = (_Actor * max(1, len(actors)))()
+    for k, (osc, p0, p1, base) in enumerate(actors):
+        arr[k].scene = osc._h
+        arr[k].pose0[:] = [float(v) for v in np.asarray(p0, dtype=np.float64).ravel()]
+        arr[k].pose1[:] = [float(v) for v in np.asarray(p1, dtype=np.float64).ravel()]
+        arr[k].id_base = int(base)
+
+    def arrg(a, shape):
+        if a is None:
+            return None
+        return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+    gr, gd = arrg(g_rgb, (m, 3)), arrg(g_depth, (m,))
+    go, gi = arrg(g_opacity, (m,)), arrg(g_intensity, (m,))
+    opt = _opts(t_min, background, want_intensity, brute_force)
+    out = []
+    for fn in ([lib.orc_backward_actors] + ([lib.orc_backward_actors_bound] if bound else [])):
+        g = np.zeros((oscene.n, 32))
+        ag = [np.zeros((a[0].n, 32)) for a in actors]
+        ptrs = (C.c_void_p * max(1, len(actors)))(*[a.ctypes.data for a in ag])
+        st = fn(oscene._h, C.cast(arr, C.c_void_p), len(actors), C.byref(s), C.byref(opt),
+                _ptr(idx), m, _ptr(gr), _ptr(gd), _ptr(go), _ptr(gi), _ptr(g),
+                C.cast(ptrs, C.c_void_p))
+        if st != 0:
+            raise RuntimeError(f"oracle actor backward failed: {st}")
+        out.append((g, ag))
+    del keep
+    return out if bound else out[0]
 
 
 def voxel_at(oscene, X) -> int:

@@ -1179,6 +1179,323 @@ int orc_render_actors(const orc_scene* s, const orc_actor* actors, int32_t n_act
   return 0;
 }
 
+/* Adjoint of the actor render (Sec. IV-A: actors are fitted with the scene).
+ * The composited hits of one ray, in orc_render_actors' order, with every
+ * per-hit quantity the adjoint needs; the field of a hit is evaluated in its
+ * own frame (local coordinates and SH direction of that frame). */
+typedef struct {
+  int64_t n;
+  int32_t *frame, *vox;
+  double *tm, *dl, *sig, *lin, *c, *io, *alpha, *T, *w, *x, *dir, *edge;
+  double t_end;
+} actor_record;
+
+static void ar_free(actor_record* a) {
+  free(a->frame);
+  free(a->vox);
+  free(a->tm);
+  free(a->dl);
+  free(a->sig);
+  free(a->lin);
+  free(a->c);
+  free(a->io);
+  free(a->alpha);
+  free(a->T);
+  free(a->w);
+  free(a->x);
+  free(a->dir);
+  free(a->edge);
+}
+
+static void actor_ray(const orc_scene* s, const orc_actor* actors, int32_t n_actors,
+                      const orc_opts* opt, const double o[3], const double d[3], double tn,
+                      double tf, double sfr, actor_record* ar) {
+  const int nf = 1 + n_actors;
+  double* fo = (double*)malloc((size_t)nf * 3 * sizeof(double));
+  double* fd = (double*)malloc((size_t)nf * 3 * sizeof(double));
+  for (int a = 0; a < 3; ++a) {
+    fo[a] = o[a];
+    fd[a] = d[a];
+  }
+  for (int k = 0; k < n_actors; ++k) {
+    double R[9], t[3], rel[3];
+    interp_pose(actors[k].pose0, actors[k].pose1, sfr, R, t);
+    for (int a = 0; a < 3; ++a) rel[a] = o[a] - t[a];
+    for (int c = 0; c < 3; ++c) {
+      fo[3 * (1 + k) + c] = R[c] * rel[0] + R[3 + c] * rel[1] + R[6 + c] * rel[2];
+      fd[3 * (1 + k) + c] = R[c] * d[0] + R[3 + c] * d[1] + R[6 + c] * d[2];
+    }
+  }
+  mhit* mh = NULL;
+  int64_t nh = 0, ch = 0;
+  for (int f = 0; f < nf; ++f) {
+    const orc_scene* sc = f == 0 ? s : actors[f - 1].scene;
+    hitvec hv = {0, 0, 0};
+    trace_vec(sc, fo + 3 * f, fd + 3 * f, tn, tf, opt->brute_force, &hv);
+    for (int64_t q = 0; q < hv.n; ++q) {
+      if (nh == ch) {
+        ch = ch ? 2 * ch : 64;
+        mh = (mhit*)realloc(mh, (size_t)ch * sizeof(mhit));
+      }
+      mh[nh].frame = f;
+      mh[nh].voxel = hv.h[q].voxel;
+      mh[nh].t_in = hv.h[q].t_in;
+      mh[nh].t_out = hv.h[q].t_out;
+      mh[nh].key = dmax(hv.h[q].t_in, tn);
+      ++nh;
+    }
+    free(hv.h);
+  }
+  if (nh > 1) qsort(mh, (size_t)nh, sizeof(mhit), mhit_cmp);
+  size_t M = (size_t)(nh ? nh : 1);
+  ar->frame = (int32_t*)malloc(M * sizeof(int32_t));
+  ar->vox = (int32_t*)malloc(M * sizeof(int32_t));
+  ar->tm = (double*)malloc(M * sizeof(double));
+  ar->dl = (double*)malloc(M * sizeof(double));
+  ar->sig = (double*)malloc(M * sizeof(double));
+  ar->lin = (double*)malloc(M * sizeof(double));
+  ar->c = (double*)malloc(3 * M * sizeof(double));
+  ar->io = (double*)malloc(M * sizeof(double));
+  ar->alpha = (double*)malloc(M * sizeof(double));
+  ar->T = (double*)malloc(M * sizeof(double));
+  ar->w = (double*)malloc(M * sizeof(double));
+  ar->x = (double*)malloc(3 * M * sizeof(double));
+  ar->dir = (double*)malloc(3 * M * sizeof(double));
+  ar->edge = (double*)malloc(M * sizeof(double));
+  double T = 1.0;
+  int64_t k = 0;
+  for (; k < nh; ++k) {
+    const int f = mh[k].frame;
+    const orc_scene* sc = f == 0 ? s : actors[f - 1].scene;
+    const double* of = fo + 3 * f;
+    const double* df = fd + 3 * f;
+    double lo[3], hi[3], e;
+    voxel_box(sc, mh[k].voxel, lo, hi, &e);
+    double a = dmax(mh[k].t_in, tn), b = dmin(mh[k].t_out, tf);
+    double tm = 0.5 * (a + b), dl = b - a;
+    double x[3];
+    for (int ax = 0; ax < 3; ++ax)
+      x[ax] = (of[ax] + tm * df[ax] - 0.5 * (lo[ax] + hi[ax])) / (0.5 * e);
+    const double* rec = sc->params + (size_t)REC * mh[k].voxel;
+    double sig, c[3], io;
+    orc_field(rec, sc->mode, x, df, &sig, c, &io);
+    if (!opt->want_intensity) io = 0.0;
+    double lin = rec[3];
+    for (int q = 0; q < 3; ++q) lin += rec[q] * x[q];
+    double alpha = 1.0 - exp(-sig * dl); /* Eq. 4 */
+    ar->frame[k] = f;
+    ar->vox[k] = mh[k].voxel;
+    ar->tm[k] = tm;
+    ar->dl[k] = dl;
+    ar->sig[k] = sig;
+    ar->lin[k] = lin;
+    ar->io[k] = io;
+    ar->alpha[k] = alpha;
+    ar->T[k] = T;
+    ar->w[k] = T * alpha; /* Eq. 3 */
+    ar->edge[k] = e;
+    for (int q = 0; q < 3; ++q) {
+      ar->c[3 * k + q] = c[q];
+      ar->x[3 * k + q] = x[q];
+      ar->dir[3 * k + q] = df[q];
+    }
+    T = T * (1.0 - alpha);
+    if (opt->t_min > 0 && T < opt->t_min) {
+      ++k;
+      break;
+    }
+  }
+  ar->n = k;
+  ar->t_end = T;
+  free(mh);
+  free(fo);
+  free(fd);
+}
+
+/* grad (static, n*32) and actor_grads[k] (actor k's n_k*32, NULL = not
+ * wanted) += d/d(record scalars) of sum_r g_r . outputs_r of the actor render,
+ * by the same adjoint as orc_backward: with q_k = (c_k, t_mid,k, 1, iota_k),
+ *   dL/dtau_k = T_{k+1} (g . q_k) - sum_{j>k} w_j (g . q_j) - T_end (g_rgb . bg),
+ * then the chain rule through the hit's field in its own frame. */
+int orc_backward_actors(const orc_scene* s, const orc_actor* actors, int32_t n_actors,
+                        const orc_sensor* sen, const orc_opts* opt, const int64_t* idx, int64_t m,
+                        const double* g_rgb, const double* g_depth, const double* g_opacity,
+                        const double* g_intensity, double* grad, double* const* actor_grads) {
+  if (sen->width <= 0 || sen->height <= 0 || n_actors < 0) return 1;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t r = idx ? idx[i] : i;
+    double o[3], d[3], tn, tf, tau;
+    uint8_t valid;
+    one_ray(sen, r, o, d, &tn, &tf, &tau, &valid);
+    if (!valid) continue;
+    double gc[3] = {0, 0, 0}, gd = 0, go = 0, gi = 0;
+    if (g_rgb)
+      for (int q = 0; q < 3; ++q) gc[q] = g_rgb[3 * i + q];
+    if (g_depth) gd = g_depth[i];
+    if (g_opacity) go = g_opacity[i];
+    if (g_intensity && opt->want_intensity) gi = g_intensity[i];
+    actor_record ar;
+    actor_ray(s, actors, n_actors, opt, o, d, tn, tf, time_fraction(sen, tau), &ar);
+    int64_t n = ar.n;
+    double* gq = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double* suf = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+    for (int64_t k = 0; k < n; ++k)
+      gq[k] = gc[0] * ar.c[3 * k] + gc[1] * ar.c[3 * k + 1] + gc[2] * ar.c[3 * k + 2] +
+              gd * ar.tm[k] + go + gi * ar.io[k];
+    double acc = 0;
+    for (int64_t k = n - 1; k >= 0; --k) {
+      suf[k] = acc; /* sum_{j>k} w_j gq_j */
+      acc += ar.w[k] * gq[k];
+    }
+    double gbg = gc[0] * opt->background[0] + gc[1] * opt->background[1] +
+                 gc[2] * opt->background[2];
+    for (int64_t k = 0; k < n; ++k) {
+      const int f = ar.frame[k];
+      const orc_scene* sc = f == 0 ? s : actors[f - 1].scene;
+      double* gbase = f == 0 ? grad : actor_grads[f - 1];
+      if (!gbase) continue;
+      const double* rec = sc->params + (size_t)REC * ar.vox[k];
+      double* gr = gbase + (size_t)REC * ar.vox[k];
+      double gam[4];
+      orc_sh_basis(ar.dir + 3 * k, gam);
+      double Tn = ar.T[k] * (1.0 - ar.alpha[k]);
+      double dtau = Tn * gq[k] - suf[k] - ar.t_end * gbg;
+      double dsig = dtau * ar.dl[k];
+      const double* x = ar.x + 3 * k;
+      double xh[4] = {x[0], x[1], x[2], 1.0};
+      if (sc->mode == 0) {
+        for (int a = 0; a < 4; ++a) ADD(&gr[a], dsig * ar.sig[k] * xh[a]);
+      } else {
+        double a = rec[25], b = rec[26], sp = ar.lin[k];
+        double ex = exp(-fabs(sp) / b);
+        double ds = dsig * (a / (2.0 * b)) * ex;
+        for (int q = 0; q < 4; ++q) ADD(&gr[q], ds * xh[q]);
+        ADD(&gr[25], dsig * ar.sig[k] / a);
+        ADD(&gr[26], dsig * (-a * sp * ex / (2.0 * b * b)));
+      }
+      for (int q = 0; q < 3; ++q) {
+        double cq = ar.c[3 * k + q];
+        double dz = ar.w[k] * gc[q] * cq * (1.0 - cq);
+        for (int a = 0; a < 3; ++a) ADD(&gr[4 + 3 * q + a], dz * x[a]);
+        for (int b = 0; b < 4; ++b) ADD(&gr[13 + 4 * q + b], dz * gam[b]);
+      }
+      if (opt->want_intensity) {
+        double io = ar.io[k];
+        double dz = ar.w[k] * gi * io * (1.0 - io);
+        for (int a = 0; a < 4; ++a) ADD(&gr[27 + a], dz * xh[a]);
+      }
+    }
+    free(gq);
+    free(suf);
+    ar_free(&ar);
+  }
+  return 0;
+}
+
+/* The rounding bound of orc_backward_bound for orc_backward_actors' sums
+ * (same construction; distances and edges are those of each hit's frame). */
+int orc_backward_actors_bound(const orc_scene* s, const orc_actor* actors, int32_t n_actors,
+                              const orc_sensor* sen, const orc_opts* opt, const int64_t* idx,
+                              int64_t m, const double* g_rgb, const double* g_depth,
+                              const double* g_opacity, const double* g_intensity, double* bound,
+                              double* const* actor_bounds) {
+  if (sen->width <= 0 || sen->height <= 0 || n_actors < 0) return 1;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t r = idx ? idx[i] : i;
+    double o[3], d[3], tn, tf, tau;
+    uint8_t valid;
+    one_ray(sen, r, o, d, &tn, &tf, &tau, &valid);
+    if (!valid) continue;
+    double gc[3] = {0, 0, 0}, gd = 0, go = 0, gi = 0;
+    if (g_rgb)
+      for (int q = 0; q < 3; ++q) gc[q] = g_rgb[3 * i + q];
+    if (g_depth) gd = g_depth[i];
+    if (g_opacity) go = g_opacity[i];
+    if (g_intensity && opt->want_intensity) gi = g_intensity[i];
+    actor_record ar;
+    actor_ray(s, actors, n_actors, opt, o, d, tn, tf, time_fraction(sen, tau), &ar);
+    int64_t n = ar.n;
+    size_t N = (size_t)(n ? n : 1);
+    double* gqa = (double*)malloc(N * sizeof(double));
+    double* kap = (double*)malloc(N * sizeof(double));
+    double* phi = (double*)malloc(N * sizeof(double));
+    double* tk = (double*)malloc(N * sizeof(double));
+    double* wm = (double*)malloc(N * sizeof(double));
+    double lam = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      const int f = ar.frame[k];
+      const orc_scene* sc = f == 0 ? s : actors[f - 1].scene;
+      const double* rec = sc->params + (size_t)REC * ar.vox[k];
+      tk[k] = ar.tm[k] + 0.5 * ar.dl[k];
+      kap[k] = 1.0 + 2.0 * tk[k] / ar.edge[k];
+      double ws = fabs(rec[0]) + fabs(rec[1]) + fabs(rec[2]);
+      lam += ar.sig[k] * tk[k] + ar.sig[k] * ar.dl[k] * kap[k] * ws;
+      gqa[k] = fabs(gc[0] * ar.c[3 * k]) + fabs(gc[1] * ar.c[3 * k + 1]) +
+               fabs(gc[2] * ar.c[3 * k + 2]) + fabs(gd * ar.tm[k]) + fabs(go) +
+               fabs(gi * ar.io[k]);
+    }
+    double sabs = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      const int f = ar.frame[k];
+      const orc_scene* sc = f == 0 ? s : actors[f - 1].scene;
+      const double* rec = sc->params + (size_t)REC * ar.vox[k];
+      double sl = 0.0;
+      for (int q = 0; q < 3; ++q) sl += fabs(rec[q]);
+      for (int q = 4; q < 13; ++q) sl += fabs(rec[q]);
+      for (int q = 27; q < 30; ++q) sl += fabs(rec[q]);
+      phi[k] = kap[k] * (1.0 + sl) + lam;
+      wm[k] = ar.w[k] * phi[k] + ar.T[k] * ar.sig[k] * tk[k];
+      sabs += wm[k] * gqa[k];
+    }
+    double gbga = fabs(gc[0] * opt->background[0]) + fabs(gc[1] * opt->background[1]) +
+                  fabs(gc[2] * opt->background[2]);
+    for (int64_t k = 0; k < n; ++k) {
+      const int f = ar.frame[k];
+      const orc_scene* sc = f == 0 ? s : actors[f - 1].scene;
+      double* bbase = f == 0 ? bound : actor_bounds[f - 1];
+      if (!bbase) continue;
+      const double* rec = sc->params + (size_t)REC * ar.vox[k];
+      double* bd = bbase + (size_t)REC * ar.vox[k];
+      double gam[4];
+      orc_sh_basis(ar.dir + 3 * k, gam);
+      double dtm = ar.T[k] * gqa[k] + sabs + ar.t_end * gbga;
+      double dsm = dtm * (ar.dl[k] * phi[k] + tk[k]);
+      const double* x = ar.x + 3 * k;
+      double xa[4] = {fabs(x[0]) + 1.0, fabs(x[1]) + 1.0, fabs(x[2]) + 1.0, 2.0};
+      if (sc->mode == 0) {
+        for (int a = 0; a < 4; ++a) ADD(&bd[a], dsm * ar.sig[k] * xa[a]);
+      } else {
+        double a = rec[25], b = rec[26], sp = ar.lin[k];
+        double ex = exp(-fabs(sp) / b);
+        double ds = dsm * (a / (2.0 * b)) * ex * (1.0 + kap[k] / b);
+        for (int q = 0; q < 4; ++q) ADD(&bd[q], ds * xa[q]);
+        ADD(&bd[25], dsm * ar.sig[k] / a);
+        ADD(&bd[26], dsm * a * (fabs(sp) + 1.0) * ex / (2.0 * b * b) * (1.0 + kap[k] / b));
+      }
+      for (int q = 0; q < 3; ++q) {
+        double cq = ar.c[3 * k + q];
+        double dz = wm[k] * fabs(gc[q]) * cq * (1.0 - cq);
+        for (int a = 0; a < 3; ++a) ADD(&bd[4 + 3 * q + a], dz * xa[a]);
+        for (int b = 0; b < 4; ++b) ADD(&bd[13 + 4 * q + b], dz * fabs(gam[b]));
+      }
+      if (opt->want_intensity) {
+        double io = ar.io[k];
+        double dz = wm[k] * fabs(gi) * io * (1.0 - io);
+        for (int a = 0; a < 4; ++a) ADD(&bd[27 + a], dz * xa[a]);
+      }
+    }
+    free(gqa);
+    free(kap);
+    free(phi);
+    free(tk);
+    free(wm);
+    ar_free(&ar);
+  }
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Densification (Sec. III-C)                                                */
 /* ------------------------------------------------------------------------ */

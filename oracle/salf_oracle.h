@@ -163,6 +163,21 @@ int orc_render_actors(const orc_scene* s, const orc_actor* actors, int32_t n_act
                       const orc_sensor* sen, const orc_opts* opt, const int64_t* idx, int64_t m,
                       const orc_outputs* out);
 
+/* Adjoint of orc_render_actors (actors are fitted with the scene, Sec. IV-A):
+ * grad (static scene, n*32) and actor_grads[k] (actor k's n_k*32; NULL =
+ * not wanted) += d/d(record scalars) of sum_r g_r . outputs_r (raydrop is
+ * not part of the actor render).  The _bound variant accumulates the FP32
+ * rounding bound of orc_backward_bound for the same sums. */
+int orc_backward_actors(const orc_scene* s, const orc_actor* actors, int32_t n_actors,
+                        const orc_sensor* sen, const orc_opts* opt, const int64_t* idx, int64_t m,
+                        const double* g_rgb, const double* g_depth, const double* g_opacity,
+                        const double* g_intensity, double* grad, double* const* actor_grads);
+int orc_backward_actors_bound(const orc_scene* s, const orc_actor* actors, int32_t n_actors,
+                              const orc_sensor* sen, const orc_opts* opt, const int64_t* idx,
+                              int64_t m, const double* g_rgb, const double* g_depth,
+                              const double* g_opacity, const double* g_intensity, double* bound,
+                              double* const* actor_bounds);
+
 #ifdef __cplusplus
 }
 #endif
