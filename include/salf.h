@@ -392,6 +392,30 @@ salf_status salf_render_rays_actors(salf_scene* scene, const salf_actor* actors,
                                     void* stream);
 
 /*
+ * Adjoint of salf_render_rays_actors (actors are fitted together with the
+ * static scene, Sec. IV-A): the gradients of the merged walk's compositing,
+ * transmittance recomputed front to back as in salf_render_backward.  `saved`
+ * is the R x 8 array that salf_render_rays_actors wrote with the same scene,
+ * actors, poses, sensor and options; d_rgb, d_depth, d_opacity, d_intensity
+ * are dL/d(outputs) as for salf_render_backward (raydrop is not part of the
+ * actor render).  d_params (static scene, n x 32 FP32, input order, device;
+ * NULL = the scene's own gradient buffer, see salf_scene_params) and
+ * actor_d_params[k] (actor k's n_k x 32 FP32, input order of its voxels,
+ * device; a NULL array or entry = no gradient for that actor) are
+ * ACCUMULATED (+=); all 16-byte aligned.  The per-call actor table and tile
+ * lists live in the scene-owned actor workspace (calls on one scene are
+ * ordered on the GPU).  Asynchronous on `stream`.  Errors: INVALID, OVERLAP,
+ * OOM, CUDA.
+ */
+salf_status salf_render_backward_actors(salf_scene* scene, const salf_actor* actors,
+                                        int32_t n_actors, const salf_sensor* sensor,
+                                        const salf_render_opts* opts, const float* saved,
+                                        const float* d_rgb, const float* d_depth,
+                                        const float* d_opacity, const float* d_intensity,
+                                        float* d_params, float* const* actor_d_params,
+                                        void* stream);
+
+/*
  * Densification and pruning (Sec. III-C), in two calls.
  * salf_scene_refine_plan decides per voxel, from `grads` (n x 32 FP32,
  * dL/d(record scalars), input order, device, 16-byte aligned) and

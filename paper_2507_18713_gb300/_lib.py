@@ -118,6 +118,9 @@ SIGNATURES = {
     "salf_render_backward": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts), c_void_p,
                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p], c_int32),
+    "salf_render_backward_actors": ([c_void_p, C.POINTER(Actor), c_int32, C.POINTER(Sensor),
+                                     C.POINTER(RenderOpts), c_void_p, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "salf_scene_check": ([c_void_p], c_int32),
     "salf_serve_create": ([c_void_p, C.c_size_t, c_int32, C.POINTER(c_void_p)], c_int32),
     "salf_serve_submit": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),

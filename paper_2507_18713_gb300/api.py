@@ -463,6 +463,45 @@ class Scene:
         return d_params
 
 
+    def backward_actors(self, sensor: dict, actors, saved, d_rgb=None, d_depth=None,
+                        d_opacity=None, d_intensity=None, d_params=None, actor_d_params=None,
+                        t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False,
+                        stream=None):
+        """salf_render_backward_actors: the adjoint of render_actors (same
+        actors, poses, sensor and options; `saved` from that render).  Returns
+        (d_params (n, 32), [actor k's (n_k, 32)]) float32, accumulated into
+        the given tensors if any (d_params="scene": the scene's own buffer)."""
+        dev = torch.device("cuda", self.ctx.device)
+        own = isinstance(d_params, str) and d_params == "scene"
+        if own:
+            d_params = self.grads_view()
+        elif d_params is None:
+            d_params = torch.zeros((self.n, 32), dtype=torch.float32, device=dev)
+        if actor_d_params is None:
+            actor_d_params = [torch.zeros((a[0].n, 32), dtype=torch.float32, device=dev)
+                              for a in actors]
+
+        def ptr(t):
+            return None if t is None else t.contiguous().data_ptr()
+
+        keep = [t.contiguous() for t in (d_rgb, d_depth, d_opacity, d_intensity) if t is not None]
+        arr = (L.Actor * max(1, len(actors)))()
+        for k, (sc, p0, p1, base) in enumerate(actors):
+            arr[k].actor = sc._h
+            arr[k].pose0[:] = [float(v) for v in np.asarray(p0, dtype=np.float64).ravel()]
+            arr[k].pose1[:] = [float(v) for v in np.asarray(p1, dtype=np.float64).ravel()]
+            arr[k].id_base = int(base)
+        aptr = (C.c_void_p * max(1, len(actors)))(*[ptr(t) for t in actor_d_params])
+        s = sensor_struct(sensor, keep)
+        op = opts_struct(t_min, background, want_intensity, 0)
+        L.check(L.load().salf_render_backward_actors(
+            self._h, arr, len(actors), C.byref(s), C.byref(op), saved.data_ptr(), ptr(d_rgb),
+            ptr(d_depth), ptr(d_opacity), ptr(d_intensity), None if own else d_params.data_ptr(),
+            C.cast(aptr, C.c_void_p), _stream_ptr(stream)),
+            "salf_render_backward_actors")
+        return d_params, actor_d_params
+
+
 class RenderFn(torch.autograd.Function):
     """Differentiable render: (params) -> (rgb, depth, opacity).
 

@@ -354,6 +354,220 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_for
   }
 }
 
+// Adjoint of one hit, composited in the merge order: with the ray's saved
+// totals (gQ = g . Q), the prefix sum Pk of w g.q and T in front of the hit,
+//   dL/dtau = T_next (g . q) - (gQ - Pk) - T_end (g_rgb . background),
+// chained through the hit's field in its own frame (Eq. 1-2, 5-6), then
+// added to the record's gradient row (16-byte atomics).  Returns T_next.
+template <int DT, int MODE>
+__device__ __forceinline__ float adjoint_hit(const Walk& w, const Hit& h, const float4* rec,
+                                             const int* order, int n, float* dparams,
+                                             int* status, bool want_int, const float gam[4],
+                                             const float g[6], float gQ, float Tend, float gbg,
+                                             float T, float* Pk) {
+  if (h.vox < 0 || h.vox >= n) {  // never expected: record it and skip the hit
+    atomicOr(status, SALF_DEVERR_BOUNDS);
+    return T;
+  }
+  const float tm = 0.5f * (h.tin + h.tout);
+  const float dl = h.tout - h.tin;
+  float x[3];
+  local_coords(w, h, tm, x);
+  Field f;
+  const GlobalRec src{rec + (size_t)h.vox * RecordLayout<DT>::kChunks};
+  field_eval_src<DT, MODE>(src, want_int, x, gam, f);
+  const float e = __expf(-f.sig * dl);
+  const float wgt = T * (1.f - e);
+  const float gq = g[0] * f.c[0] + g[1] * f.c[1] + g[2] * f.c[2] + g[3] * tm + g[4] + g[5] * f.io;
+  *Pk = fmaf(wgt, gq, *Pk);
+  const float Tn = T * e;
+  if (!dparams) return Tn;
+  const float dtau = Tn * gq - (gQ - *Pk) - Tend * gbg;
+  const float dsig = dtau * dl;
+  float gr[32];
+  const float xh[4] = {x[0], x[1], x[2], 1.f};
+  float gs;  // dL/d(geometry value W . [x, 1])
+  gr[25] = gr[26] = 0.f;
+  if (MODE == SALF_FIELD_EXP) {
+    gs = dsig * f.sig;
+  } else {
+    const float ex = __expf(-fabsf(f.lin) / f.b);
+    gs = dsig * (f.a / (2.f * f.b)) * ex;
+    gr[25] = dsig * f.sig / f.a;
+    gr[26] = -dsig * f.a * f.lin * ex / (2.f * f.b * f.b);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) gr[q] = gs * xh[q];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    const float dz = wgt * g[ch] * f.c[ch] * (1.f - f.c[ch]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gr[4 + 3 * ch + a] = dz * xh[a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) gr[13 + 4 * ch + b] = dz * gam[b];
+  }
+  const float di = want_int ? wgt * g[5] * f.io * (1.f - f.io) : 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) gr[27 + q] = di * xh[q];
+  gr[31] = 0.f;
+  const int key = __ldg(&order[h.vox]);
+  if (key < 0 || key >= n) {
+    atomicOr(status, SALF_DEVERR_BOUNDS);
+    return Tn;
+  }
+  float4* dst = reinterpret_cast<float4*>(dparams) + (size_t)key * 8;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (q < 7 || want_int)
+      atomicAdd(dst + q, make_float4(gr[4 * q], gr[4 * q + 1], gr[4 * q + 2], gr[4 * q + 3]));
+  return Tn;
+}
+
+// Adjoint of k_forward_actors on the tiles whose rays may meet an actor: the
+// same merge walk (the same hits in the same order, the first n_visits of
+// them, n_visits from the saved totals), each hit's gradient row going to the
+// static scene's buffer or its actor's.
+template <int DT, int MODE>
+__global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_backward_actors(
+    const __grid_constant__ LaunchParams P, const ActorDev* __restrict__ actors, int n_actors,
+    const unsigned* __restrict__ masks) {
+  const int warp = blockIdx.x * kActorWarps + (threadIdx.x >> 5);
+  if (warp >= P.total_tiles) return;
+  const int lane = threadIdx.x & 31;
+  const ReqDev& Q = P.req[0];
+  const DevScene& S = P.S;
+  int tile = warp - Q.tile_begin;
+  if (Q.tile_list) {
+    if (tile >= __ldg(Q.tile_count)) return;
+    tile = __ldg(&Q.tile_list[tile]);
+  }
+  if (tile < 0 || tile >= Q.n_tiles) {  // never expected: record it and skip the tile
+    if (lane == 0) atomicOr(S.status, SALF_DEVERR_BOUNDS);
+    return;
+  }
+  int u0, v0;
+  tile_origin(Q, tile, &u0, &v0);
+  const int u = u0 + lane % Q.tile_w;
+  const int v = v0 + lane / Q.tile_w;
+  const bool in_img = (u >= 0) && (v >= 0) && (u < Q.W) && (v < Q.H);
+  const int ray = v * Q.W + u;
+
+  Ray r;
+  Walk ws;
+  ws.alive = false;
+  r.valid = false;
+  r.s = 0.f;
+  r.d[0] = r.d[1] = r.d[2] = 0.f;
+  float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float gQ = 0.f, Tend = 1.f;
+  int nv = 0;
+  if (in_img) {
+    gen_ray(Q, S, u, v, ray, r);
+    walk_init(S, r, ws);
+    const float4* sp = reinterpret_cast<const float4*>(Q.bsaved) + 2 * (size_t)ray;
+    const float4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
+    if (Q.g_rgb) {
+      g[0] = __ldg(Q.g_rgb + 3 * (size_t)ray);
+      g[1] = __ldg(Q.g_rgb + 3 * (size_t)ray + 1);
+      g[2] = __ldg(Q.g_rgb + 3 * (size_t)ray + 2);
+    }
+    if (Q.g_depth) g[3] = __ldg(Q.g_depth + ray);
+    if (Q.g_opacity) g[4] = __ldg(Q.g_opacity + ray);
+    if (Q.g_int && Q.want_int) g[5] = __ldg(Q.g_int + ray);
+    gQ = g[0] * s0.x + g[1] * s0.y + g[2] * s0.z + g[3] * s0.w + g[4] * s1.x + g[5] * s1.y;
+    Tend = s1.z;
+    nv = r.valid ? (int)s1.w : 0;
+  }
+  float gam_s[4];
+  sh_basis(r.d, gam_s);
+  const float gbg = g[0] * Q.bg[0] + g[1] * Q.bg[1] + g[2] * Q.bg[2];
+
+  // 1. entry-sorted actor intervals along the ray (as in the forward)
+  float iv_in[kMaxIntervals];
+  int iv_k[kMaxIntervals];
+  int ni = 0;
+  if (in_img && r.valid) {
+    for (int wd = 0; wd * 32 < n_actors; ++wd) {
+      unsigned bits = __ldg(&masks[(size_t)tile * kMaskWords + wd]);
+      while (bits) {
+        const int k = wd * 32 + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const ActorDev& A = actors[k];
+        float a0;
+        if (!may_meet(A, r) || !box_interval(A, r, &a0)) continue;
+        int pos = ni < kMaxIntervals ? ni : kMaxIntervals - 1;
+        if (ni == kMaxIntervals) {
+          atomicOr(S.status, SALF_DEVERR_ACTOR_CAP);
+          if (a0 >= iv_in[pos]) continue;
+        } else {
+          ++ni;
+        }
+        while (pos > 0 && iv_in[pos - 1] > a0) {
+          iv_in[pos] = iv_in[pos - 1];
+          iv_k[pos] = iv_k[pos - 1];
+          --pos;
+        }
+        iv_in[pos] = a0;
+        iv_k[pos] = k;
+      }
+    }
+  }
+
+  // 2. the forward's merge walk, with the adjoint of each composited hit
+  const bool want_int = Q.want_int != 0;
+  const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
+  float T = 1.f, Pk = 0.f;
+  int done = 0;
+  Hit hs, ha;
+  bool hs_ok = false, ha_ok = false;
+  Walk wa;
+  wa.alive = false;
+  float gam_a[4] = {0.f, 0.f, 0.f, 0.f};
+  int cur = -1, nxt = 0;
+  bool live = in_img && r.valid && nv > 0;
+  for (;;) {
+    if (!__any_sync(0xffffffffu, live)) break;
+    if (!live) continue;
+    if (cur >= 0 && !ha_ok && !wa.alive) cur = -1;
+    const bool start_next =
+        cur < 0 && nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)));
+    if (!hs_ok && ws.alive) {
+      hs_ok = next_hit(S, ws, hs, budget);
+    } else if (start_next) {
+      cur = iv_k[nxt++];
+      if (cur < 0 || cur >= n_actors) {  // never expected: record it and stop the ray
+        atomicOr(S.status, SALF_DEVERR_BOUNDS);
+        live = false;
+        continue;
+      }
+      actor_walk(actors[cur], r, wa, gam_a);
+      ha_ok = false;
+    } else if (cur >= 0 && !ha_ok && wa.alive) {
+      ha_ok = next_hit(actors[cur].S, wa, ha, budget);
+    }
+    const bool s_res = hs_ok || !ws.alive;
+    const bool a_res = cur < 0 ? !(nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin))))
+                               : (ha_ok || !wa.alive);
+    if (!(s_res && a_res)) continue;
+    if (ha_ok && (!hs_ok || ha.tin < hs.tin)) {
+      const ActorDev& A = actors[cur];
+      T = adjoint_hit<DT, MODE>(wa, ha, reinterpret_cast<const float4*>(A.S.params), A.S.order,
+                                A.S.n, A.dparams, S.status, want_int, gam_a, g, gQ, Tend, gbg,
+                                T, &Pk);
+      ha_ok = false;
+    } else if (hs_ok) {
+      T = adjoint_hit<DT, MODE>(ws, hs, reinterpret_cast<const float4*>(S.params), S.order,
+                                S.n, Q.d_params, S.status, want_int, gam_s, g, gQ, Tend, gbg,
+                                T, &Pk);
+      hs_ok = false;
+    } else {
+      if (cur < 0 && nxt >= ni) live = false;
+      continue;
+    }
+    if (++done >= nv) live = false;  // the forward composited exactly nv hits
+  }
+}
+
 template <int DT, int MODE>
 void launch_actors(const LaunchParams& P, const ActorDev* actors, int n, const unsigned* masks,
                    bool dump, cudaStream_t st) {
@@ -366,6 +580,22 @@ void launch_actors(const LaunchParams& P, const ActorDev* actors, int n, const u
 }
 
 }  // namespace
+
+cudaError_t salf_launch_backward_actors(const LaunchParams& P, const ActorDev* actors,
+                                        int n_actors, const unsigned* masks, cudaStream_t st) {
+  const int blocks = (P.total_tiles + kActorWarps - 1) / kActorWarps;
+  if (blocks == 0) return cudaSuccess;
+  const int dt = P.S.dtype, md = P.S.mode;
+  if (dt == SALF_F32 && md == SALF_FIELD_EXP)
+    k_backward_actors<SALF_F32, SALF_FIELD_EXP><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n_actors, masks);
+  else if (dt == SALF_F32)
+    k_backward_actors<SALF_F32, SALF_FIELD_SDF><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n_actors, masks);
+  else if (md == SALF_FIELD_EXP)
+    k_backward_actors<SALF_BF16, SALF_FIELD_EXP><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n_actors, masks);
+  else
+    k_backward_actors<SALF_BF16, SALF_FIELD_SDF><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n_actors, masks);
+  return cudaGetLastError();
+}
 
 cudaError_t salf_launch_classify(const LaunchParams& P, const ActorDev* actors, int n_actors,
                                  int* lists, int* counts, unsigned* masks, cudaStream_t st) {

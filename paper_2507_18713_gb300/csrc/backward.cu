@@ -39,8 +39,17 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
   const int lane = threadIdx.x & 31;
   const ReqDev& Q = P.req[find_request(P, warp)];
   const DevScene& S = P.S;
+  int tile = warp - Q.tile_begin;
+  if (Q.tile_list) {  // a subset of the tiles (the actor adjoint takes the rest)
+    if (tile >= __ldg(Q.tile_count)) return;
+    tile = __ldg(&Q.tile_list[tile]);
+    if (tile < 0 || tile >= Q.n_tiles) {  // never expected: record it and skip the tile
+      if (lane == 0) atomicOr(S.status, SALF_DEVERR_BOUNDS);
+      return;
+    }
+  }
   int u0, v0;
-  tile_origin(Q, warp - Q.tile_begin, &u0, &v0);
+  tile_origin(Q, tile, &u0, &v0);
   const int u = u0 + lane % Q.tile_w;
   const int v = v0 + lane / Q.tile_w;
   const bool in_img = (u < Q.W) && (v < Q.H);

@@ -138,7 +138,9 @@ extern "C" salf_status salf_scene_check(salf_scene* s) {
     cudaMemset(s->dev.status, 0, sizeof(int));
     g_err = "device status word " + std::to_string(flag) +
             ((flag & SALF_DEVERR_STEP_CAP) ? " (traversal step bound reached)" : "") +
-            ((flag & SALF_DEVERR_SDF_AB) ? " (SDF record with a <= 0 or b <= 0)" : "");
+            ((flag & SALF_DEVERR_SDF_AB) ? " (SDF record with a <= 0 or b <= 0)" : "") +
+            ((flag & SALF_DEVERR_ACTOR_CAP) ? " (a ray met more actor boxes than it holds)" : "") +
+            ((flag & SALF_DEVERR_BOUNDS) ? " (an adjoint index outside its buffers, skipped)" : "");
     return SALF_ERR_DEVICE;
   }
   return SALF_OK;
@@ -713,46 +715,21 @@ static bool obb_overlap(const Obb& A, const Obb& B, double tol) {
   return true;
 }
 
-extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor* actors,
-                                              int32_t n_actors, const salf_sensor* sen,
-                                              const salf_render_opts* opts,
-                                              const salf_outputs* out, void* stream) {
-  if (!sc || !sen || !out || n_actors < 0 || (n_actors > 0 && !actors)) {
-    g_err = "salf_render_rays_actors: null argument or negative count";
-    return SALF_ERR_INVALID;
-  }
-  if (n_actors > SALF_MAX_ACTORS) {
-    g_err = "salf_render_rays_actors: more than SALF_MAX_ACTORS actors";
-    return SALF_ERR_INVALID;
-  }
-  const salf_render_opts o = opts ? *opts : default_opts();
-  if (out->on_host || out->ray_dump || out->steps || out->raydrop) {
-    g_err = "salf_render_rays_actors: device outputs only (no ray_dump, steps or raydrop)";
-    return SALF_ERR_INVALID;
-  }
-  if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
-      !(o.visits_cap > 0 && out->visits)) {
-    g_err = "salf_render_rays_actors: no output requested";
-    return SALF_ERR_INVALID;
-  }
-  if (o.visits_cap > 0 && (!out->visits || !out->visit_count)) {
-    g_err = "salf_render_rays_actors: visits_cap > 0 needs visits and visit_count";
-    return SALF_ERR_INVALID;
-  }
-  if (misaligned(out->saved, 16)) {
-    g_err = "salf_render_rays_actors: saved must be 16-byte aligned";
-    return SALF_ERR_INVALID;
-  }
+// Checks of an actor list (shared by the forward and the adjoint): every actor
+// scene matches the static scene's device, dtype and field mode, poses are
+// finite, and the actors' boxes are pairwise disjoint at t0 and at t1.
+static salf_status check_actors(const salf_scene* sc, const salf_actor* actors, int32_t n_actors,
+                                const char* who) {
   for (int k = 0; k < n_actors; ++k) {
     const salf_scene* a = actors[k].actor;
     if (!a || a->device != sc->device || a->dtype != sc->dtype || a->mode != sc->mode) {
-      g_err = "salf_render_rays_actors: actor " + std::to_string(k) +
+      g_err = std::string(who) + ": actor " + std::to_string(k) +
               " is null or differs from the scene in device, dtype or field mode";
       return SALF_ERR_INVALID;
     }
     for (int q = 0; q < 12; ++q)
       if (!std::isfinite(actors[k].pose0[q]) || !std::isfinite(actors[k].pose1[q])) {
-        g_err = "salf_render_rays_actors: non-finite actor pose";
+        g_err = std::string(who) + ": non-finite actor pose";
         return SALF_ERR_INVALID;
       }
   }
@@ -765,34 +742,21 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
         const double* pi = t ? actors[i].pose1 : actors[i].pose0;
         const double* pj = t ? actors[j].pose1 : actors[j].pose0;
         if (obb_overlap(actor_obb(actors[i].actor, pi), actor_obb(actors[j].actor, pj), 1e-9)) {
-          g_err = "salf_render_rays_actors: boxes of actors " + std::to_string(i) + " and " +
+          g_err = std::string(who) + ": boxes of actors " + std::to_string(i) + " and " +
                   std::to_string(j) + " overlap at t" + std::to_string(t);
           return SALF_ERR_OVERLAP;
         }
       }
     }
   }
-  cudaError_t e;
-  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
-  LaunchParams P;
-  std::memset(&P, 0, sizeof(P));
-  P.S = sc->dev;
-  P.n_req = 1;
-  ReqDev& r = P.req[0];
-  salf_status st = salf_prepare_request(sc, sen, &o, &r);
-  if (st != SALF_OK) return st;
-  salf_request_tiling(&r, sen, 0);  // this path walks whole rays
-  P.total_tiles = r.n_tiles;
-  P.step_budget = salf_step_budget();
-  r.rgb = out->rgb;
-  r.depth = out->depth;
-  r.opacity = out->opacity;
-  r.intensity = out->intensity;
-  r.saved = out->saved;
-  r.valid = out->valid;
-  r.vcount = out->visit_count;
-  r.visits = out->visits;
+  return SALF_OK;
+}
 
+// The actor table of one request (FP64 -> FP32 constants), skipping empty
+// actors; actor k's adjoint buffer is dparams[k] when dparams is not null.
+static std::vector<ActorDev> actor_table(const salf_actor* actors, int32_t n_actors,
+                                         const salf_sensor* sen, const ReqDev& r,
+                                         float* const* dparams) {
   // per-actor constants (FP64 -> FP32)
   std::vector<ActorDev> ad;
   ad.reserve((size_t)n_actors);
@@ -843,8 +807,68 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
     A.radius = (float)(std::sqrt(h2) + std::sqrt(cn2) * ang * ang / 8.0 +
                        1e-3 * (1.0 + std::sqrt(c0n2)));
     A.id_base = actors[k].id_base;
+    A.dparams = dparams ? dparams[k] : nullptr;
     ad.push_back(A);
   }
+  return ad;
+}
+
+extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor* actors,
+                                              int32_t n_actors, const salf_sensor* sen,
+                                              const salf_render_opts* opts,
+                                              const salf_outputs* out, void* stream) {
+  if (!sc || !sen || !out || n_actors < 0 || (n_actors > 0 && !actors)) {
+    g_err = "salf_render_rays_actors: null argument or negative count";
+    return SALF_ERR_INVALID;
+  }
+  if (n_actors > SALF_MAX_ACTORS) {
+    g_err = "salf_render_rays_actors: more than SALF_MAX_ACTORS actors";
+    return SALF_ERR_INVALID;
+  }
+  const salf_render_opts o = opts ? *opts : default_opts();
+  if (out->on_host || out->ray_dump || out->steps || out->raydrop) {
+    g_err = "salf_render_rays_actors: device outputs only (no ray_dump, steps or raydrop)";
+    return SALF_ERR_INVALID;
+  }
+  if (!out->rgb && !out->depth && !out->opacity && !out->intensity && !out->saved && !out->valid &&
+      !(o.visits_cap > 0 && out->visits)) {
+    g_err = "salf_render_rays_actors: no output requested";
+    return SALF_ERR_INVALID;
+  }
+  if (o.visits_cap > 0 && (!out->visits || !out->visit_count)) {
+    g_err = "salf_render_rays_actors: visits_cap > 0 needs visits and visit_count";
+    return SALF_ERR_INVALID;
+  }
+  if (misaligned(out->saved, 16)) {
+    g_err = "salf_render_rays_actors: saved must be 16-byte aligned";
+    return SALF_ERR_INVALID;
+  }
+  {
+    const salf_status cs = check_actors(sc, actors, n_actors, "salf_render_rays_actors");
+    if (cs != SALF_OK) return cs;
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  LaunchParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.S = sc->dev;
+  P.n_req = 1;
+  ReqDev& r = P.req[0];
+  salf_status st = salf_prepare_request(sc, sen, &o, &r);
+  if (st != SALF_OK) return st;
+  salf_request_tiling(&r, sen, 0);  // this path walks whole rays
+  P.total_tiles = r.n_tiles;
+  P.step_budget = salf_step_budget();
+  r.rgb = out->rgb;
+  r.depth = out->depth;
+  r.opacity = out->opacity;
+  r.intensity = out->intensity;
+  r.saved = out->saved;
+  r.valid = out->valid;
+  r.vcount = out->visit_count;
+  r.visits = out->visits;
+
+  const std::vector<ActorDev> ad = actor_table(actors, n_actors, sen, r, nullptr);
   const int na = (int)ad.size();
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(sc->actor_mu);
@@ -913,6 +937,119 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
         (e = cudaStreamWaitEvent(cs, sc->actor_join, 0)) != cudaSuccess)
       return salf_cuda_fail(e, "actor join");
   }
+  if ((e = cudaEventRecord(sc->actor_done, cs)) != cudaSuccess)
+    return salf_cuda_fail(e, "actor event");
+  return SALF_OK;
+}
+
+extern "C" salf_status salf_render_backward_actors(
+    salf_scene* sc, const salf_actor* actors, int32_t n_actors, const salf_sensor* sen,
+    const salf_render_opts* opts, const float* saved, const float* d_rgb, const float* d_depth,
+    const float* d_opacity, const float* d_intensity, float* d_params,
+    float* const* actor_d_params, void* stream) {
+  if (!sc || !sen || !saved || n_actors < 0 || (n_actors > 0 && !actors)) {
+    g_err = "salf_render_backward_actors: null argument or negative count";
+    return SALF_ERR_INVALID;
+  }
+  if (n_actors > SALF_MAX_ACTORS) {
+    g_err = "salf_render_backward_actors: more than SALF_MAX_ACTORS actors";
+    return SALF_ERR_INVALID;
+  }
+  if (!d_params) {  // the scene's own gradient buffer
+    std::lock_guard<std::mutex> lk(sc->grads_mu);
+    d_params = sc->grads;
+    if (!d_params) {
+      g_err = "salf_render_backward_actors: d_params is NULL and salf_scene_params has not "
+              "created the scene's gradient buffer";
+      return SALF_ERR_INVALID;
+    }
+  }
+  if (misaligned(saved, 16) || misaligned(d_params, 16)) {
+    g_err = "salf_render_backward_actors: saved and d_params must be 16-byte aligned";
+    return SALF_ERR_INVALID;
+  }
+  for (int k = 0; actor_d_params && k < n_actors; ++k)
+    if (misaligned(actor_d_params[k], 16)) {
+      g_err = "salf_render_backward_actors: actor gradient buffers must be 16-byte aligned";
+      return SALF_ERR_INVALID;
+    }
+  {
+    const salf_status cs = check_actors(sc, actors, n_actors, "salf_render_backward_actors");
+    if (cs != SALF_OK) return cs;
+  }
+  const salf_render_opts o = opts ? *opts : default_opts();
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  LaunchParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.S = sc->dev;
+  P.n_req = 1;
+  ReqDev& r = P.req[0];
+  salf_status st = salf_prepare_request(sc, sen, &o, &r);
+  if (st != SALF_OK) return st;
+  salf_request_tiling(&r, sen, 0);  // the forward's tiles (whole rays)
+  P.total_tiles = r.n_tiles;
+  P.step_budget = salf_step_budget();
+  r.vcap = 0;
+  r.bsaved = saved;
+  r.g_rgb = d_rgb;
+  r.g_depth = d_depth;
+  r.g_opacity = d_opacity;
+  r.g_int = d_intensity;
+  r.d_params = d_params;
+  const std::vector<ActorDev> ad = actor_table(actors, n_actors, sen, r, actor_d_params);
+  const int na = (int)ad.size();
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (na == 0) {  // the static adjoint alone
+    if ((e = salf_launch_backward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "backward launch");
+    return SALF_OK;
+  }
+  std::lock_guard<std::mutex> lk(sc->actor_mu);
+  if (!sc->actor_done) {
+    if ((e = cudaEventCreateWithFlags(&sc->actor_done, cudaEventDisableTiming)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor event");
+  } else if ((e = cudaStreamWaitEvent(cs, sc->actor_done, 0)) != cudaSuccess) {
+    return salf_cuda_fail(e, "actor event wait");
+  }
+  const size_t table_bytes = (((size_t)na * sizeof(ActorDev)) + 255) & ~(size_t)255;
+  const size_t mask_bytes = (size_t)r.n_tiles * (SALF_MAX_ACTORS / 32) * sizeof(unsigned);
+  const size_t bytes = table_bytes + mask_bytes + (2 * (size_t)r.n_tiles + 2) * sizeof(int);
+  if (sc->actor_buf_bytes < bytes) {
+    if ((e = cudaEventSynchronize(sc->actor_done)) != cudaSuccess)
+      return salf_cuda_fail(e, "actor sync");
+    if (sc->actor_buf) cudaFree(sc->actor_buf);
+    sc->actor_buf = nullptr;
+    sc->actor_buf_bytes = 0;
+    const size_t grow = bytes + bytes / 4;
+    if (cudaMalloc(&sc->actor_buf, grow) != cudaSuccess) {
+      cudaGetLastError();
+      g_err = "salf_render_backward_actors: out of device memory";
+      return SALF_ERR_OOM;
+    }
+    sc->actor_buf_bytes = grow;
+  }
+  ActorDev* dact = static_cast<ActorDev*>(sc->actor_buf);
+  unsigned* masks = reinterpret_cast<unsigned*>(static_cast<char*>(sc->actor_buf) + table_bytes);
+  int* lists = reinterpret_cast<int*>(static_cast<char*>(sc->actor_buf) + table_bytes + mask_bytes);
+  int* counts = lists + 2 * (size_t)r.n_tiles;
+  if ((e = cudaMemcpyAsync(dact, ad.data(), (size_t)na * sizeof(ActorDev), cudaMemcpyHostToDevice,
+                           cs)) != cudaSuccess)
+    return salf_cuda_fail(e, "actor table upload");
+  if ((e = cudaMemsetAsync(counts, 0, 2 * sizeof(int), cs)) != cudaSuccess)
+    return salf_cuda_fail(e, "actor tile counts");
+  // the forward's split: tiles whose rays may meet an actor take the merge
+  // walk's adjoint, the others the static adjoint
+  if ((e = salf_launch_classify(P, dact, na, lists, counts, masks, cs)) != cudaSuccess)
+    return salf_cuda_fail(e, "tile classification");
+  LaunchParams Ps = P;
+  Ps.req[0].tile_list = lists;
+  Ps.req[0].tile_count = counts;
+  if ((e = salf_launch_backward(Ps, cs)) != cudaSuccess) return salf_cuda_fail(e, "backward launch");
+  LaunchParams Pa = P;
+  Pa.req[0].tile_list = lists + r.n_tiles;
+  Pa.req[0].tile_count = counts + 1;
+  if ((e = salf_launch_backward_actors(Pa, dact, na, masks, cs)) != cudaSuccess)
+    return salf_cuda_fail(e, "actor backward launch");
   if ((e = cudaEventRecord(sc->actor_done, cs)) != cudaSuccess)
     return salf_cuda_fail(e, "actor event");
   return SALF_OK;

@@ -39,6 +39,7 @@
 #define SALF_DEVERR_STEP_CAP 1  // a traversal loop reached its iteration bound
 #define SALF_DEVERR_SDF_AB 2    // an SDF record has a <= 0 or b <= 0
 #define SALF_DEVERR_ACTOR_CAP 4 // a ray met more actor boxes than it can hold
+#define SALF_DEVERR_BOUNDS 8    // an adjoint kernel met an index outside its buffers (skipped)
 
 // Read-only view of a built scene, passed to kernels by value.
 //
@@ -163,6 +164,7 @@ struct ActorDev {
   float inv_sfin;       // actor finest cells per metre
   float box_lo[3], box_hi[3];  // tight box of the actor's voxels (canonical m)
   int id_base;          // visit ids of its voxels: id_base + input index
+  float* dparams;       // adjoint: dL/d(record scalars) of its voxels (input order), or null
 };
 
 struct LaunchParams {
@@ -261,3 +263,8 @@ cudaError_t salf_launch_classify(const LaunchParams& P, const ActorDev* actors, 
 salf_status salf_raster_run(salf_scene* sc, const ReqDev& r, double fx, double fy,
                             salf_raster_stats* stats, cudaStream_t st);
 cudaError_t salf_launch_backward(const LaunchParams& P, cudaStream_t st);
+// Adjoint of the actor frame on the tiles listed in P.req[0].tile_list (the
+// merge walk of salf_launch_actors, gradients into d_params and each actor's
+// dparams).
+cudaError_t salf_launch_backward_actors(const LaunchParams& P, const ActorDev* actors,
+                                        int n_actors, const unsigned* masks, cudaStream_t st);
