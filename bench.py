@@ -243,46 +243,45 @@ def bench_backward(torch, P, steps, warmup, flush, peak):
     R = 960 * 640
     outs = [dict(rgb=torch.empty((R, 3), device="cuda"), saved=torch.empty((R, 8), device="cuda"))
             for _ in cams]
+    grads = [torch.empty((R, 3), device="cuda") for _ in cams]
     inv = 1.0 / (R * 3 * len(cams))
 
     def step():
+        # the 8 cameras in one forward launch and one adjoint launch
         dparams.zero_()
-        for cam, o, tg in zip(cams, outs, targets):
-            g.render(cam, outputs=("rgb",), saved=True, out=o, valid=False)
-            grad = (o["rgb"] - tg).mul_(2 * inv)
-            g.backward(cam, o["saved"], d_rgb=grad, d_params=dparams)
+        g.render_batch(cams, outputs=("rgb",), saved=True, valid=False, outs=outs)
+        for o, tg, gr in zip(outs, targets, grads):
+            torch.sub(o["rgb"], tg, out=gr).mul_(2 * inv)
+        g.backward_batch(cams, [o["saved"] for o in outs], d_rgb=grads, d_params=dparams)
 
     ms = timed_renders(torch, step, max(3, steps // 20), warmup, flush)
     g.check()
     avg = sum(ms) / len(ms)
-    # the adjoint kernel alone (one launch per camera), with its algorithmic
-    # bytes: per visit the BF16 record's 25 used scalars (50 B) and 25 FP32
-    # gradient scalars added (100 B); per ray dL/drgb (12 B) and the saved
-    # totals (32 B)
-    grads = [(o["rgb"] - tg).mul_(2 * inv) for o, tg in zip(outs, targets)]
+    # the adjoint kernel alone (one batched launch over the 8 cameras), with its
+    # algorithmic bytes: per visit the BF16 record's 25 used scalars (50 B) and
+    # 25 FP32 gradient scalars added (100 B); per ray dL/drgb (12 B) and the
+    # saved totals (32 B)
     visits = sum(int(o["saved"][:, 7].double().sum().item()) for o in outs)
-    k = [0]
-
-    def adj():
-        i = k[0] % len(cams)
-        k[0] += 1
-        g.backward(cams[i], outs[i]["saved"], d_rgb=grads[i], d_params=dparams)
-
-    ms_adj = timed_renders(torch, adj, 8 * max(3, steps // 20), warmup, flush)
+    adj = lambda: g.backward_batch(cams, [o["saved"] for o in outs], d_rgb=grads,
+                                   d_params=dparams)
+    ms_adj = timed_renders(torch, adj, max(3, steps // 20), warmup, flush)
     avg_adj = sum(ms_adj) / len(ms_adj)
-    b_adj = visits / len(cams) * (B_FIELD_EXP_BF16 + 4 * 25) + R * (12 + 32)
+    b_adj = visits * (B_FIELD_EXP_BF16 + 4 * 25) + len(cams) * R * (12 + 32)
     ach = b_adj / (avg_adj * 1e-3) / 1e9
     return dict(workload="8 pinhole 960x640, driving scene 1,000,000 voxels (seed 4), BF16 "
-                "records, FP32 grads, MSE vs U[0,1] targets",
+                "records, FP32 grads, MSE vs U[0,1] targets; salf_render_rays_batch + "
+                "salf_render_backward_batch (one launch each for the 8 cameras)",
                 ms_per_step=avg, mrays_s=len(cams) * R / (avg * 1e-3) / 1e6,
-                adjoint=dict(kernel="k_backward<BF16,EXP>", ms_per_camera=avg_adj,
+                adjoint=dict(kernel="k_backward<BF16,EXP>, the 8 cameras in one launch",
+                             ms_per_launch=avg_adj, ms_per_camera=avg_adj / len(cams),
                              visits_per_ray=visits / (len(cams) * R),
                              roofline=dict(bound="hbm", achieved=ach, peak=peak, unit="GB/s",
                                            frac=ach / peak, bytes_per_launch=b_adj,
                                            note="per visit 50 B BF16 record + 100 B of gradient "
                                                 "scalars (25 x 4 B), per ray 12 B dL/drgb + "
                                                 "32 B saved totals; visits counted by the "
-                                                "forward kernel")))
+                                                "forward kernel; bytes and time of the one "
+                                                "launch")))
 
 
 def bench_refine(torch, P, flush):

@@ -269,6 +269,37 @@ salf_status salf_render_rays(salf_scene* scene, const salf_sensor* sensor,
                              void* stream);
 
 /*
+ * Render n sensors in one launch (n <= 24 per launch; more are split into
+ * launches of 24), e.g. the cameras of one training step.  Each sensor's
+ * outputs are those of a lone salf_render_rays call with the same options
+ * (rays are independent); one launch lets the sensors' longest rays overlap
+ * instead of paying their serial latency once per sensor.  sensors[i] and
+ * outs[i] as for salf_render_rays; outputs must be device memory (on_host,
+ * visits, ray_dump, steps and max_alpha are rejected).  `opts` applies to
+ * every sensor.  Asynchronous on `stream`.  Errors: INVALID, CUDA.
+ */
+salf_status salf_render_rays_batch(salf_scene* scene, int32_t n, const salf_sensor* sensors,
+                                   const salf_render_opts* opts, const salf_outputs* outs,
+                                   void* stream);
+
+/*
+ * The adjoint of a salf_render_rays_batch call (or of n salf_render_rays
+ * calls) in one launch: for sensor i, saved[i] is its R_i x 8 saved array and
+ * d_rgb[i], d_depth[i], d_opacity[i], d_intensity[i] its dL/d(outputs) (the
+ * arrays of pointers may be NULL, and so may their entries: zero).  d_params
+ * (n_voxels x 32 FP32, input order, device, 16-byte aligned; NULL = the
+ * scene's own gradient buffer) is ACCUMULATED (+=) with the sum over the
+ * sensors.  Raydrop gradients are not supported here.  Asynchronous on
+ * `stream`.  Errors: INVALID, CUDA.
+ */
+salf_status salf_render_backward_batch(salf_scene* scene, int32_t n, const salf_sensor* sensors,
+                                       const salf_render_opts* opts, const float* const* saved,
+                                       const float* const* d_rgb, const float* const* d_depth,
+                                       const float* const* d_opacity,
+                                       const float* const* d_intensity, float* d_params,
+                                       void* stream);
+
+/*
  * salf_render_rays for host output buffers, without any device allocation.
  * The paper has no counterpart: this serves callers that cannot let a library
  * allocate device memory -- real-time loops that cannot absorb an

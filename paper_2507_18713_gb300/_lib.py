@@ -121,6 +121,11 @@ SIGNATURES = {
     "salf_render_backward_actors": ([c_void_p, C.POINTER(Actor), c_int32, C.POINTER(Sensor),
                                      C.POINTER(RenderOpts), c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "salf_render_rays_batch": ([c_void_p, c_int32, C.POINTER(Sensor), C.POINTER(RenderOpts),
+                                C.POINTER(Outputs), c_void_p], c_int32),
+    "salf_render_backward_batch": ([c_void_p, c_int32, C.POINTER(Sensor), C.POINTER(RenderOpts),
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p], c_int32),
     "salf_scene_check": ([c_void_p], c_int32),
     "salf_serve_create": ([c_void_p, C.c_size_t, c_int32, C.POINTER(c_void_p)], c_int32),
     "salf_serve_submit": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),

@@ -246,6 +246,74 @@ class Scene:
             res["_keep"] = keep
         return res
 
+    def render_batch(self, sensors, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                     want_intensity=False, outputs=("rgb", "depth", "opacity"), saved=False,
+                     valid=True, stream=None, outs=None, ray_segments: int = 0) -> list:
+        """salf_render_rays_batch: every sensor in one launch (list of output
+        dicts of CUDA tensors, new or the given `outs`); asynchronous."""
+        dev = torch.device("cuda", self.ctx.device)
+        n = len(sensors)
+        res = []
+        arr = (L.Outputs * max(1, n))()
+        sarr = (L.Sensor * max(1, n))()
+        keep: list = []
+        for i, sen in enumerate(sensors):
+            R = n_rays(sen)
+            d = {} if outs is None else dict(outs[i])
+            shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,),
+                      "raydrop": (R,)}
+            for k in outputs:
+                if k not in d:
+                    d[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
+            if saved and "saved" not in d:
+                d["saved"] = torch.empty((R, 8), dtype=torch.float32, device=dev)
+            if valid and "valid" not in d:
+                d["valid"] = torch.empty((R,), dtype=torch.uint8, device=dev)
+            for k in ("rgb", "depth", "opacity", "intensity", "saved", "valid", "raydrop"):
+                if k in d:
+                    setattr(arr[i], k, d[k].data_ptr())
+            sarr[i] = sensor_struct(sen, keep)
+            res.append(d)
+        op = opts_struct(t_min, background, want_intensity, 0, ray_segments)
+        L.check(L.load().salf_render_rays_batch(self._h, n, sarr, C.byref(op), arr,
+                                                _stream_ptr(stream)), "salf_render_rays_batch")
+        if keep:
+            res[0]["_keep"] = keep
+        return res
+
+    def backward_batch(self, sensors, saved, d_rgb=None, d_depth=None, d_opacity=None,
+                       d_intensity=None, d_params=None, t_min=1e-4, background=(0.0, 0.0, 0.0),
+                       want_intensity=False, stream=None):
+        """salf_render_backward_batch: the adjoint of every sensor in one launch,
+        summed into d_params (n, 32) float32 (new, given, or "scene").  saved
+        and the d_* are lists (one tensor or None per sensor) or None."""
+        dev = torch.device("cuda", self.ctx.device)
+        own = isinstance(d_params, str) and d_params == "scene"
+        if own:
+            d_params = self.grads_view()
+        elif d_params is None:
+            d_params = torch.zeros((self.n, 32), dtype=torch.float32, device=dev)
+        n = len(sensors)
+        keep: list = []
+
+        def ptrs(lst):
+            if lst is None:
+                return None
+            ts = [None if t is None else t.contiguous() for t in lst]
+            keep.extend(t for t in ts if t is not None)
+            return C.cast((C.c_void_p * max(1, n))(*[None if t is None else t.data_ptr()
+                                                    for t in ts]), C.c_void_p)
+
+        sarr = (L.Sensor * max(1, n))()
+        for i, sen in enumerate(sensors):
+            sarr[i] = sensor_struct(sen, keep)
+        op = opts_struct(t_min, background, want_intensity, 0)
+        L.check(L.load().salf_render_backward_batch(
+            self._h, n, sarr, C.byref(op), ptrs(saved), ptrs(d_rgb), ptrs(d_depth),
+            ptrs(d_opacity), ptrs(d_intensity), None if own else d_params.data_ptr(),
+            _stream_ptr(stream)), "salf_render_backward_batch")
+        return d_params
+
     def render_raster(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
                       want_intensity=False, visits_cap=0, outputs=("rgb", "depth", "opacity"),
                       saved=False, valid=True, stream=None, out: dict | None = None,

@@ -1055,6 +1055,122 @@ extern "C" salf_status salf_render_backward_actors(
   return SALF_OK;
 }
 
+extern "C" salf_status salf_render_rays_batch(salf_scene* sc, int32_t n,
+                                              const salf_sensor* sensors,
+                                              const salf_render_opts* opts,
+                                              const salf_outputs* outs, void* stream) {
+  if (!sc || n < 0 || (n > 0 && (!sensors || !outs))) {
+    g_err = "salf_render_rays_batch: null argument or negative count";
+    return SALF_ERR_INVALID;
+  }
+  const salf_render_opts o = opts ? *opts : default_opts();
+  if (o.visits_cap > 0) {
+    g_err = "salf_render_rays_batch: visit lists are not supported";
+    return SALF_ERR_INVALID;
+  }
+  for (int i = 0; i < n; ++i) {
+    const salf_outputs& out = outs[i];
+    if (out.on_host || out.visits || out.visit_count || out.ray_dump || out.steps ||
+        out.max_alpha) {
+      g_err = "salf_render_rays_batch: device outputs only (no visits, ray_dump, steps or max_alpha)";
+      return SALF_ERR_INVALID;
+    }
+    if (!out.rgb && !out.depth && !out.opacity && !out.intensity && !out.saved && !out.valid &&
+        !out.raydrop) {
+      g_err = "salf_render_rays_batch: no output requested for sensor " + std::to_string(i);
+      return SALF_ERR_INVALID;
+    }
+    if (misaligned(out.saved, 16)) {
+      g_err = "salf_render_rays_batch: saved must be 16-byte aligned";
+      return SALF_ERR_INVALID;
+    }
+  }
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  for (int b = 0; b < n; b += SALF_MAX_BATCH) {
+    LaunchParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.S = sc->dev;
+    P.step_budget = salf_step_budget();
+    for (int i = b; i < std::min(n, b + SALF_MAX_BATCH); ++i) {
+      ReqDev& r = P.req[P.n_req++];
+      const salf_status st = salf_prepare_request(sc, &sensors[i], &o, &r);
+      if (st != SALF_OK) return st;
+      r.rgb = outs[i].rgb;
+      r.depth = outs[i].depth;
+      r.opacity = outs[i].opacity;
+      r.intensity = outs[i].intensity;
+      r.saved = outs[i].saved;
+      r.valid = outs[i].valid;
+      r.raydrop = outs[i].raydrop;
+      r.tile_begin = P.total_tiles;
+      P.total_tiles += r.n_tiles;
+    }
+    if ((e = salf_launch_forward(P, cs)) != cudaSuccess) return salf_cuda_fail(e, "forward launch");
+  }
+  return SALF_OK;
+}
+
+extern "C" salf_status salf_render_backward_batch(
+    salf_scene* sc, int32_t n, const salf_sensor* sensors, const salf_render_opts* opts,
+    const float* const* saved, const float* const* d_rgb, const float* const* d_depth,
+    const float* const* d_opacity, const float* const* d_intensity, float* d_params,
+    void* stream) {
+  if (!sc || n < 0 || (n > 0 && (!sensors || !saved))) {
+    g_err = "salf_render_backward_batch: null argument or negative count";
+    return SALF_ERR_INVALID;
+  }
+  if (!d_params) {  // the scene's own gradient buffer
+    std::lock_guard<std::mutex> lk(sc->grads_mu);
+    d_params = sc->grads;
+    if (!d_params) {
+      g_err = "salf_render_backward_batch: d_params is NULL and salf_scene_params has not created "
+              "the scene's gradient buffer";
+      return SALF_ERR_INVALID;
+    }
+  }
+  if (misaligned(d_params, 16)) {
+    g_err = "salf_render_backward_batch: d_params must be 16-byte aligned";
+    return SALF_ERR_INVALID;
+  }
+  for (int i = 0; i < n; ++i)
+    if (!saved[i] || misaligned(saved[i], 16)) {
+      g_err = "salf_render_backward_batch: saved[" + std::to_string(i) +
+              "] is null or not 16-byte aligned";
+      return SALF_ERR_INVALID;
+    }
+  const salf_render_opts o = opts ? *opts : default_opts();
+  cudaError_t e;
+  if ((e = cudaSetDevice(sc->device)) != cudaSuccess) return salf_cuda_fail(e, "cudaSetDevice");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  auto pick = [&](const float* const* a, int i) { return a ? a[i] : nullptr; };
+  for (int b = 0; b < n; b += SALF_MAX_BATCH) {
+    LaunchParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.S = sc->dev;
+    P.step_budget = salf_step_budget();
+    for (int i = b; i < std::min(n, b + SALF_MAX_BATCH); ++i) {
+      ReqDev& r = P.req[P.n_req++];
+      const salf_status st = salf_prepare_request(sc, &sensors[i], &o, &r);
+      if (st != SALF_OK) return st;
+      salf_request_tiling(&r, &sensors[i], 0);  // the adjoint walks whole rays
+      r.vcap = 0;
+      r.bsaved = saved[i];
+      r.g_rgb = pick(d_rgb, i);
+      r.g_depth = pick(d_depth, i);
+      r.g_opacity = pick(d_opacity, i);
+      r.g_int = pick(d_intensity, i);
+      r.d_params = d_params;
+      r.tile_begin = P.total_tiles;
+      P.total_tiles += r.n_tiles;
+    }
+    if ((e = salf_launch_backward(P, cs)) != cudaSuccess)
+      return salf_cuda_fail(e, "backward launch");
+  }
+  return SALF_OK;
+}
+
 extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* sen,
                                             const salf_render_opts* opts, const float* saved,
                                             const float* d_rgb, const float* d_depth,
