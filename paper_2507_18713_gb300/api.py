@@ -599,6 +599,34 @@ class RenderFn(torch.autograd.Function):
         return own.clone(), None, None, None, None
 
 
+class RenderBatchFn(torch.autograd.Function):
+    """Differentiable render of several sensors in one launch each way:
+    (params) -> (rgb_0, depth_0, opacity_0, rgb_1, ...).  forward uploads
+    `params` into the scene and calls salf_render_rays_batch; backward calls
+    salf_render_backward_batch into the scene's own gradient buffer and hands
+    autograd a copy."""
+
+    @staticmethod
+    def forward(ctx, params, scene: Scene, sensors, t_min: float = 1e-4,
+                background=(0.0, 0.0, 0.0)):
+        scene.update_params(params)
+        outs = scene.render_batch(sensors, t_min=t_min, background=background, saved=True,
+                                  outputs=("rgb", "depth", "opacity"))
+        ctx.scene, ctx.sensors, ctx.t_min, ctx.background = scene, sensors, t_min, background
+        ctx.save_for_backward(*[o["saved"] for o in outs])
+        return tuple(t for o in outs for t in (o["rgb"], o["depth"], o["opacity"]))
+
+    @staticmethod
+    def backward(ctx, *grads):
+        saved = list(ctx.saved_tensors)
+        own = ctx.scene.grads_view()
+        own.zero_()
+        ctx.scene.backward_batch(ctx.sensors, saved, d_rgb=list(grads[0::3]),
+                                 d_depth=list(grads[1::3]), d_opacity=list(grads[2::3]),
+                                 t_min=ctx.t_min, background=ctx.background, d_params="scene")
+        return own.clone(), None, None, None, None
+
+
 class Server:
     """Continuous-batching render server (salf_serve_*)."""
 

@@ -331,3 +331,26 @@ def test_batched_render_and_adjoint_equal_per_sensor_calls(salf):
     g.check()
     assert float(ref.abs().max()) > 0
     assert torch.allclose(one, ref, rtol=1e-5, atol=1e-6)
+
+
+def test_render_batch_fn_matches_render_fn(salf):
+    """RenderBatchFn (one launch each way) gives the outputs of RenderFn per
+    sensor and the summed gradient."""
+    sc = synth.random_multilevel_scene(seed=8, max_level=2, dims=(5, 4, 3), p_occ=0.8)
+    g = salf.Scene(sc)
+    sensors = [synth.pinhole(32, 24, 70.0, synth.camera_pose_looking((-1.9, 0.25, 0.9), 0.1)),
+               synth.pinhole(20, 16, 80.0, synth.camera_pose_looking((-2.0, 0.6, 1.0), -0.2))]
+    w = [torch.rand(s["width"] * s["height"], 3, generator=torch.Generator().manual_seed(k)).cuda()
+         for k, s in enumerate(sensors)]
+    p1 = torch.tensor(sc.params, dtype=torch.float32, device="cuda", requires_grad=True)
+    outs = salf.RenderBatchFn.apply(p1, g, sensors, 0.0)
+    sum((o * wi).sum() for o, wi in zip(outs[0::3], w)).backward()
+    p2 = torch.tensor(sc.params, dtype=torch.float32, device="cuda", requires_grad=True)
+    loss = 0.0
+    for s, wi, o in zip(sensors, w, outs[0::3]):
+        rgb, _, _ = salf.RenderFn.apply(p2, g, s, 0.0)
+        assert torch.equal(rgb, o)
+        loss = loss + (rgb * wi).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    assert torch.allclose(p1.grad, p2.grad, rtol=1e-5, atol=1e-6)
