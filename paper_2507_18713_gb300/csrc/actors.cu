@@ -319,6 +319,9 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_for
     } else if (cur >= 0 && !ha_ok && wa.alive) {
       ha_ok = next_hit(actors[cur].S, wa, ha, budget);
     }
+    // an actor walk that ended this round (or opened empty) leaves the next
+    // interval to be weighed against the pending static hit
+    if (cur >= 0 && !ha_ok && !wa.alive) cur = -1;
     const bool s_res = hs_ok || !ws.alive;
     const bool a_res = cur < 0 ? !(nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin))))
                                : (ha_ok || !wa.alive);
@@ -545,6 +548,9 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_bac
     } else if (cur >= 0 && !ha_ok && wa.alive) {
       ha_ok = next_hit(actors[cur].S, wa, ha, budget);
     }
+    // an actor walk that ended this round (or opened empty) leaves the next
+    // interval to be weighed against the pending static hit
+    if (cur >= 0 && !ha_ok && !wa.alive) cur = -1;
     const bool s_res = hs_ok || !ws.alive;
     const bool a_res = cur < 0 ? !(nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin))))
                                : (ha_ok || !wa.alive);

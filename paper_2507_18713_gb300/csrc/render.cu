@@ -58,20 +58,6 @@
 
 using namespace salf;
 
-// Products of the transmittances of the spans of a ray (lanes k = 0..K-1 of a
-// group of K): *inc = T_0 ... T_k, *ex = T_0 ... T_k-1 (1 for k = 0).  The
-// association order is fixed, so the products only fall as the T_k fall.
-__device__ __forceinline__ void span_products(float T, int k, int K, float* inc, float* ex) {
-  float p = T;
-  for (int off = 1; off < K; off <<= 1) {
-    const float y = __shfl_up_sync(0xffffffffu, p, off, K);
-    if (k >= off) p *= y;
-  }
-  const float e = __shfl_up_sync(0xffffffffu, p, 1, K);
-  *inc = p;
-  *ex = k == 0 ? 1.f : e;
-}
-
 // RD: the variant can write the raydrop output (instantiated only for
 // batches that ask for it, so the other variants keep their code).
 template <int DT, int MODE, bool DUMP, int WPB, int MINB, bool SEG, bool RD>

@@ -714,6 +714,20 @@ __device__ __forceinline__ void write_outputs(const ReqDev& Q, int ray, bool val
   if (Q.valid) Q.valid[ray] = valid ? 1 : 0;
 }
 
+// Products of the transmittances of the spans of a ray (lanes k = 0..K-1 of a
+// group of K): *inc = T_0 ... T_k, *ex = T_0 ... T_k-1 (1 for k = 0).  The
+// association order is fixed, so the products only fall as the T_k fall.
+__device__ __forceinline__ void span_products(float T, int k, int K, float* inc, float* ex) {
+  float p = T;
+  for (int off = 1; off < K; off <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, p, off, K);
+    if (k >= off) p *= y;
+  }
+  const float e = __shfl_up_sync(0xffffffffu, p, 1, K);
+  *inc = p;
+  *ex = k == 0 ? 1.f : e;
+}
+
 // Warp tile -> request, pixel.
 __device__ __forceinline__ int find_request(const LaunchParams& P, int warp) {
   int r = 0;

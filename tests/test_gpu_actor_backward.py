@@ -95,6 +95,28 @@ def test_actor_adjoint_matches_oracle(salf, oracle_lib, kind):
     print(kind, stats)
 
 
+def test_actor_adjoint_after_an_exhausted_actor(salf, oracle_lib):
+    """Two actors in a row whose walks end in empty cells, in front of a static
+    wall: the adjoint takes the hits in the forward's entry order (the second
+    actor's before the pending wall hit)."""
+    from tests.test_gpu_actors import _front_wall_actor
+    rng = np.random.default_rng(21)
+    cells = [(10, j, k) for j in range(4) for k in range(4)]
+    params = synth.scenes.draw_params(rng, len(cells))
+    params[:, 3] -= 1.5
+    wall = synth.scenes.single_voxel_scene(params, dims=(12, 4, 4), cells=cells,
+                                           levels=[0] * len(cells), origin=(0.0, -2.0, -2.0))
+    acts = [_front_wall_actor(31), _front_wall_actor(32)]
+    tracks = [(_rigid(0.0, (3.0, 0.0, -0.4)), _rigid(0.0, (3.0, 0.0, -0.4))),
+              (_rigid(0.0, (6.0, 0.0, -0.4)), _rigid(0.0, (6.0, 0.0, -0.4)))]
+    sen = synth.pinhole(16, 12, 6.0, synth.camera_pose_looking((0.0, 0.0, 0.0), 0.0))
+    (dg, dag), (do, dao), (bo, bao) = _case(salf, oracle_lib, wall, acts, tracks, sen)
+    grad_close(dg, do, bo)
+    for a, b, c in zip(dag, dao, bao):
+        assert np.abs(b).max() > 0
+        grad_close(a, b, c)
+
+
 def test_actor_adjoint_bf16_sdf_and_early_termination(salf, oracle_lib):
     sc = synth.random_multilevel_scene(seed=4, max_level=2, dims=(6, 5, 4), p_occ=0.35, mode="sdf")
     acts = [synth.actor_shell(1.0, 0.6, 0.5, seed=10, mode="sdf"),

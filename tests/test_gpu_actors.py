@@ -219,3 +219,36 @@ def test_driving_scene_with_24_moving_actors(salf, oracle_lib, driving_actors, w
                   want_intensity=which == "lidar")
     print(which, res)
     assert res["rays_hitting_actors"] > 100
+
+
+def _front_wall_actor(seed):
+    """An actor whose tight box reaches well past its front wall (one voxel in
+    the far corner), so a ray leaves the wall and walks empty cells before its
+    walk ends: the walk then ends in a round without a hit."""
+    rng = np.random.default_rng(seed)
+    cells = [(0, j, k) for j in range(4) for k in range(4)] + [(3, 3, 3)]
+    params = synth.scenes.draw_params(rng, len(cells))
+    params[:, 3] -= 1.5
+    return synth.scenes.single_voxel_scene(params, s0=0.2, dims=(4, 4, 4), cells=cells,
+                                           levels=[0] * len(cells), origin=(-0.4, -0.4, 0.0))
+
+
+def test_actor_after_an_exhausted_actor_precedes_the_pending_static_hit(salf, oracle_lib):
+    """Two translucent actors in a row in front of a static wall: once the
+    first actor's walk ends, the second actor's box (entered before the wall)
+    must open before the pending wall hit is composited (Eq. 3-4 take the
+    hits in entry order, whichever walk found them)."""
+    rng = np.random.default_rng(21)
+    cells = [(10, j, k) for j in range(4) for k in range(4)]
+    params = synth.scenes.draw_params(rng, len(cells))
+    params[:, 3] -= 1.5  # thin wall: rays reach it with T well above t_min
+    wall = synth.scenes.single_voxel_scene(params, dims=(12, 4, 4), cells=cells,
+                                           levels=[0] * len(cells), origin=(0.0, -2.0, -2.0))
+    acts = [_front_wall_actor(31), _front_wall_actor(32)]
+    tracks = [(_rigid(0.0, (3.0, 0.0, -0.4)), _rigid(0.0, (3.0, 0.0, -0.4))),
+              (_rigid(0.0, (6.0, 0.0, -0.4)), _rigid(0.0, (6.0, 0.0, -0.4)))]
+    sen = synth.pinhole(16, 12, 6.0, synth.camera_pose_looking((0.0, 0.0, 0.0), 0.0))
+    res = _parity(salf, oracle_lib, wall, acts, tracks, sen)
+    print(res)
+    assert res["rays_hitting_actors"] > 50
+    assert res["bad_visits"] == 0
