@@ -702,11 +702,25 @@ def main():
             except Exception as e:  # an extra section never costs the headline
                 line[name] = {"error": f"{type(e).__name__}: {e}"}
 
+        def issue_of(name, r):
+            # warp instructions of the launch (ncu, at the current kernel sources)
+            # over the issue slots of its measured duration
+            try:
+                ent = json.load(open(TRAFFIC_FILE)).get(name, {})
+                if ent.get("kernel_hash") != kernel_hash(name) or not clocks.get("sm_mhz"):
+                    return
+                inst = ent["warp_inst_per_launch"]
+                r["dram_bytes_per_launch"] = ent.get("dram_bytes_per_launch")
+                r["issue_frac"] = inst / (n_sm * 4 * clocks["sm_mhz"] * 1e6 * r["ms"] * 1e-3)
+            except Exception:
+                pass
+
         def lidar_section():
             r = section(torch, P, g, driving_lidar(), max(50, args.steps // 4), args.warmup, flush,
                         B_FIELD_EXP_INT_F32, B_OUT_LIDAR, want_intensity=True)
             r["workload"] = "spinning LiDAR 128x2048, per-ray pose, intensity, same scene"
             r["roofline_frac"] = r["achieved_gbs"] / peak
+            issue_of("lidar", r)
             return r
 
         def fisheye_section():
@@ -716,6 +730,7 @@ def main():
                         B_FIELD_EXP_F32, B_OUT_CAMERA, rays_counted=n_valid)
             r["workload"] = "equidistant fisheye 1920x1080 190deg, valid rays counted"
             r["roofline_frac"] = r["achieved_gbs"] / peak
+            issue_of("fisheye", r)
             return r
 
         def raster_section():

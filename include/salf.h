@@ -45,7 +45,8 @@ typedef enum {
   SALF_ERR_TIMEOUT = 6,   /* serving: wait ran out */
   SALF_ERR_NOT_FOUND = 7, /* serving: unknown or released ticket */
   SALF_ERR_SHUTDOWN = 8,  /* serving: server is shutting down */
-  SALF_ERR_DEVICE = 9     /* a kernel reported an internal error through its status word */
+  SALF_ERR_DEVICE = 9,    /* a kernel reported an internal error through its status word */
+  SALF_ERR_IO = 10        /* a scene file could not be opened, read or written, or is malformed */
 } salf_status;
 
 typedef enum { SALF_FIELD_EXP = 0, SALF_FIELD_SDF = 1 } salf_field_mode;
@@ -545,6 +546,24 @@ salf_status salf_secondary_rays(salf_scene* scene, const salf_sensor* sensor, co
 /* Check the scene's device status word (synchronises the device).  Returns
  * SALF_ERR_DEVICE if a kernel hit an internal bound since the last check. */
 salf_status salf_scene_check(salf_scene* scene);
+
+/*
+ * Scene files (checkpoint / resume of a scene; the paper stores trained
+ * scenes, Sec. III-A: voxel keys and their records).  salf_scene_save writes
+ * the scene's grid (origin, s0, dims, max_level), field mode, storage dtype,
+ * the voxel keys (level, ijk) in input order and the current records in input
+ * order, in the storage dtype (FP32, or BF16 bits), to `path` (binary,
+ * little-endian; layout in csrc/checkpoint.cpp).  It waits for the device
+ * (every stream's work on the records ends first).  salf_scene_load reads
+ * such a file and builds the scene on ctx's device as salf_build_scene would
+ * from the same arrays: the same voxels, records (bit for bit) and outputs.
+ * The library keeps each scene's keys for this (13 bytes per voxel of device
+ * memory, counted in device_bytes).  Errors: INVALID (null arguments), IO
+ * (cannot open, read or write; wrong magic, version or size), and those of
+ * salf_build_scene (load) or CUDA (save).
+ */
+salf_status salf_scene_save(const salf_scene* scene, const char* path);
+salf_status salf_scene_load(salf_ctx* ctx, const char* path, salf_scene** out);
 
 /*
  * Serving: a host scheduler thread batches requests from many sensors over

@@ -16,9 +16,9 @@ from . import build as _build
 c_int32, c_int64, c_float, c_double, c_void_p = C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_void_p
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_OVERLAP, ERR_AGAIN, ERR_TIMEOUT, ERR_NOT_FOUND, \
-    ERR_SHUTDOWN, ERR_DEVICE = range(10)
+    ERR_SHUTDOWN, ERR_DEVICE, ERR_IO = range(11)
 STATUS_NAMES = ["OK", "INVALID", "OOM", "CUDA", "OVERLAP", "AGAIN", "TIMEOUT", "NOT_FOUND",
-                "SHUTDOWN", "DEVICE"]
+                "SHUTDOWN", "DEVICE", "IO"]
 KIND = {"pinhole": 0, "fisheye": 1, "pano": 2, "lidar": 3, "explicit": 4}
 MODE = {"exp": 0, "sdf": 1}
 DTYPE = {"f32": 0, "bf16": 1}
@@ -127,6 +127,8 @@ SIGNATURES = {
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p], c_int32),
     "salf_scene_check": ([c_void_p], c_int32),
+    "salf_scene_save": ([c_void_p, C.c_char_p], c_int32),
+    "salf_scene_load": ([c_void_p, C.c_char_p, C.POINTER(c_void_p)], c_int32),
     "salf_serve_create": ([c_void_p, C.c_size_t, c_int32, C.POINTER(c_void_p)], c_int32),
     "salf_serve_submit": ([c_void_p, C.POINTER(Sensor), C.POINTER(RenderOpts),
                            C.POINTER(C.c_uint64)], c_int32),

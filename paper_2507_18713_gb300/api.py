@@ -5,6 +5,7 @@ device memory and streams.  Marshalling only -- no rendering arithmetic here.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 import torch
@@ -151,6 +152,32 @@ class Scene:
         self.geometry = dict(origin=tuple(float(v) for v in scene.origin), s0=float(scene.s0),
                              dims=tuple(int(v) for v in scene.dims),
                              max_level=int(scene.max_level))
+
+    def save(self, path: str) -> None:
+        """salf_scene_save: grid, keys and current records to a scene file."""
+        L.check(L.load().salf_scene_save(self._h, os.fsencode(path)), "salf_scene_save")
+
+    @classmethod
+    def load(cls, path: str, ctx: Context | None = None) -> "Scene":
+        """salf_scene_load: the scene a file written by save() describes."""
+        self = cls.__new__(cls)
+        self.ctx = ctx or Context.default()
+        lib = L.load()
+        h = C.c_void_p()
+        L.check(lib.salf_scene_load(self.ctx._h, os.fsencode(path), C.byref(h)), "salf_scene_load")
+        self._h = h
+        info = L.SceneInfo()
+        L.check(lib.salf_scene_get_info(h, C.byref(info)), "salf_scene_get_info")
+        self.n = int(info.n)
+        self.mode = {v: k for k, v in L.MODE.items()}[info.mode]
+        self.dtype = {v: k for k, v in L.DTYPE.items()}[info.dtype]
+        # origin and s0 from the file's header (after the 8-byte magic and 4 int32 + 1 int64)
+        with open(path, "rb") as f:
+            f.seek(8 + 16 + 8)
+            geo = np.frombuffer(f.read(32), dtype="<f8")
+        self.geometry = dict(origin=tuple(float(v) for v in geo[:3]), s0=float(geo[3]),
+                             dims=tuple(int(v) for v in info.dims), max_level=int(info.max_level))
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

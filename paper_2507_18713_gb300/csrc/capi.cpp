@@ -52,7 +52,15 @@ extern "C" void salf_destroy(salf_ctx* ctx) { delete ctx; }
 
 extern "C" salf_status salf_build_scene(salf_ctx* ctx, const salf_scene_desc* desc,
                                         salf_scene** out) {
-  return salf_build_scene_impl(ctx, desc, out);
+  salf_status st = salf_build_scene_impl(ctx, desc, out);
+  if (st != SALF_OK) return st;
+  // the keys stay with the scene so that salf_scene_save can write it out
+  st = salf_scene_keep_keys(*out, desc);
+  if (st != SALF_OK) {
+    salf_scene_destroy(*out);
+    *out = nullptr;
+  }
+  return st;
 }
 
 extern "C" void salf_scene_destroy(salf_scene* s) {

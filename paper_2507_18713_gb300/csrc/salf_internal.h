@@ -223,6 +223,9 @@ struct salf_scene {
   // the merge kernel runs on this stream beside the ray kernel (fork / join)
   cudaStream_t actor_aux = nullptr;
   cudaEvent_t actor_fork = nullptr, actor_join = nullptr;
+  // the voxel keys in input order (device, scene-owned; salf_scene_save)
+  const uint8_t* key_level = nullptr;
+  const int32_t* key_ijk = nullptr;
 };
 
 // Implemented in the .cu / .cpp files of the library.
@@ -235,6 +238,8 @@ salf_status salf_build_scene_impl(salf_ctx* ctx, const salf_scene_desc* d, salf_
 salf_status salf_build_scene_gpu(salf_ctx* ctx, const salf_scene_desc* d, salf_scene** out);
 // A device buffer owned (and freed) by the scene.
 salf_status salf_scene_dalloc(salf_scene* s, size_t bytes, void** p);
+// Keep a copy of the build's voxel keys in the scene (for salf_scene_save).
+salf_status salf_scene_keep_keys(salf_scene* s, const salf_scene_desc* d);
 salf_status salf_prepare_request(const salf_scene* sc, const salf_sensor* sen,
                                  const salf_render_opts* opts, ReqDev* r);
 // Warp tiles of a request with 2^seg_shift lanes per ray (0: whole rays);
