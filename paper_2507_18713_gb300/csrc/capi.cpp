@@ -52,6 +52,7 @@ extern "C" void salf_destroy(salf_ctx* ctx) { delete ctx; }
 
 extern "C" salf_status salf_build_scene(salf_ctx* ctx, const salf_scene_desc* desc,
                                         salf_scene** out) {
+  SALF_RANGE("salf_build_scene");
   salf_status st = salf_build_scene_impl(ctx, desc, out);
   if (st != SALF_OK) return st;
   // the keys stay with the scene so that salf_scene_save can write it out
@@ -174,6 +175,7 @@ static salf_status ensure_staging(salf_scene* s, size_t bytes) {
 
 extern "C" salf_status salf_scene_update_params(salf_scene* s, const float* params,
                                                 int32_t on_device, void* stream) {
+  SALF_RANGE("salf_scene_update_params");
   if (!s || (!params && s->n > 0)) {
     g_err = "salf_scene_update_params: null argument";
     return SALF_ERR_INVALID;
@@ -452,6 +454,7 @@ static bool misaligned(const void* p, unsigned a) {
 extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
                                         const salf_render_opts* opts, const salf_outputs* out,
                                         void* stream) {
+  SALF_RANGE("salf_render_rays");
   if (!sc || !sen || !out) {
     g_err = "salf_render_rays: null argument";
     return SALF_ERR_INVALID;
@@ -619,6 +622,7 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
 extern "C" salf_status salf_render_raster(salf_scene* sc, const salf_sensor* sen,
                                          const salf_render_opts* opts, const salf_outputs* out,
                                          salf_raster_stats* stats, void* stream) {
+  SALF_RANGE("salf_render_raster");
   if (!sc || !sen || !out) {
     g_err = "salf_render_raster: null argument";
     return SALF_ERR_INVALID;
@@ -825,6 +829,7 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
                                               int32_t n_actors, const salf_sensor* sen,
                                               const salf_render_opts* opts,
                                               const salf_outputs* out, void* stream) {
+  SALF_RANGE("salf_render_rays_actors");
   if (!sc || !sen || !out || n_actors < 0 || (n_actors > 0 && !actors)) {
     g_err = "salf_render_rays_actors: null argument or negative count";
     return SALF_ERR_INVALID;
@@ -955,6 +960,7 @@ extern "C" salf_status salf_render_backward_actors(
     const salf_render_opts* opts, const float* saved, const float* d_rgb, const float* d_depth,
     const float* d_opacity, const float* d_intensity, float* d_params,
     float* const* actor_d_params, void* stream) {
+  SALF_RANGE("salf_render_backward_actors");
   if (!sc || !sen || !saved || n_actors < 0 || (n_actors > 0 && !actors)) {
     g_err = "salf_render_backward_actors: null argument or negative count";
     return SALF_ERR_INVALID;
@@ -1067,6 +1073,7 @@ extern "C" salf_status salf_render_rays_batch(salf_scene* sc, int32_t n,
                                               const salf_sensor* sensors,
                                               const salf_render_opts* opts,
                                               const salf_outputs* outs, void* stream) {
+  SALF_RANGE("salf_render_rays_batch");
   if (!sc || n < 0 || (n > 0 && (!sensors || !outs))) {
     g_err = "salf_render_rays_batch: null argument or negative count";
     return SALF_ERR_INVALID;
@@ -1125,6 +1132,7 @@ extern "C" salf_status salf_render_backward_batch(
     const float* const* saved, const float* const* d_rgb, const float* const* d_depth,
     const float* const* d_opacity, const float* const* d_intensity, float* d_params,
     void* stream) {
+  SALF_RANGE("salf_render_backward_batch");
   if (!sc || n < 0 || (n > 0 && (!sensors || !saved))) {
     g_err = "salf_render_backward_batch: null argument or negative count";
     return SALF_ERR_INVALID;
@@ -1185,6 +1193,7 @@ extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* s
                                             const float* d_opacity, const float* d_intensity,
                                             const float* raydrop, const float* d_raydrop,
                                             float* d_params, void* stream) {
+  SALF_RANGE("salf_render_backward");
   if (!sc || !sen || !saved) {
     g_err = "salf_render_backward: null argument";
     return SALF_ERR_INVALID;

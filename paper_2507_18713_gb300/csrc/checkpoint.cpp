@@ -71,6 +71,7 @@ salf_status salf_scene_keep_keys(salf_scene* s, const salf_scene_desc* d) {
 }
 
 extern "C" salf_status salf_scene_save(const salf_scene* s, const char* path) {
+  SALF_RANGE("salf_scene_save");
   if (!s || !path) {
     salf_set_error("salf_scene_save: null argument");
     return SALF_ERR_INVALID;
@@ -139,6 +140,7 @@ extern "C" salf_status salf_scene_save(const salf_scene* s, const char* path) {
 }
 
 extern "C" salf_status salf_scene_load(salf_ctx* ctx, const char* path, salf_scene** out) {
+  SALF_RANGE("salf_scene_load");
   if (!ctx || !path || !out) {
     salf_set_error("salf_scene_load: null argument");
     return SALF_ERR_INVALID;

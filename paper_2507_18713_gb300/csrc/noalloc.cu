@@ -68,6 +68,7 @@ salf_status salf_noalloc_setup(int device) {
 extern "C" salf_status salf_render_rays_host_noalloc(salf_scene* sc, const salf_sensor* sen,
                                                      const salf_render_opts* opts,
                                                      const salf_outputs* out, void* stream) {
+  SALF_RANGE("salf_render_rays_host_noalloc");
   if (!sc || !sen || !out) {
     salf_set_error("salf_render_rays_host_noalloc: null argument");
     return SALF_ERR_INVALID;

@@ -245,6 +245,7 @@ extern "C" salf_status salf_scene_refine_plan(salf_scene* sc, const float* grads
                                              const float* max_alpha, float split_threshold,
                                              float prune_alpha, salf_refine_counts* counts,
                                              void* stream) {
+  SALF_RANGE("salf_scene_refine_plan");
   if (!sc || !grads || !max_alpha || !counts) {
     salf_set_error("salf_scene_refine_plan: null argument");
     return SALF_ERR_INVALID;
@@ -318,6 +319,7 @@ extern "C" salf_status salf_scene_refine_plan(salf_scene* sc, const float* grads
 extern "C" salf_status salf_scene_refine_apply(salf_scene* sc, const float* params,
                                               uint8_t* level_out, int32_t* ijk_out,
                                               float* params_out, void* stream) {
+  SALF_RANGE("salf_scene_refine_apply");
   if (!sc || !params) {
     salf_set_error("salf_scene_refine_apply: null argument");
     return SALF_ERR_INVALID;
@@ -354,6 +356,7 @@ extern "C" salf_status salf_scene_refine_apply(salf_scene* sc, const float* para
 extern "C" salf_status salf_scene_reg_loss(salf_scene* sc, const float* params, float lambda_s,
                                           float lambda_alpha, float lambda_n, float* loss,
                                           float* grads, void* stream) {
+  SALF_RANGE("salf_scene_reg_loss");
   if (!sc || !params || !loss || !grads) {
     salf_set_error("salf_scene_reg_loss: null argument");
     return SALF_ERR_INVALID;

@@ -228,6 +228,27 @@ struct salf_scene {
   const int32_t* key_ijk = nullptr;
 };
 
+// NVTX ranges around the library's calls (host side: the range holds the
+// call's launches, so profilers attribute its kernels to it).  Header-only
+// NVTX3; a range costs a few nanoseconds when no tool is attached.
+#ifndef SALF_NVTX
+#define SALF_NVTX 1
+#endif
+#if SALF_NVTX
+#include <nvtx3/nvToolsExt.h>
+struct SalfRange {
+  explicit SalfRange(const char* name) { nvtxRangePushA(name); }
+  ~SalfRange() { nvtxRangePop(); }
+  SalfRange(const SalfRange&) = delete;
+  SalfRange& operator=(const SalfRange&) = delete;
+};
+#else
+struct SalfRange {
+  explicit SalfRange(const char*) {}
+};
+#endif
+#define SALF_RANGE(name) SalfRange salf_range_(name)
+
 // Implemented in the .cu / .cpp files of the library.
 void salf_set_error(const std::string& msg);
 salf_status salf_cuda_fail(cudaError_t e, const char* what);

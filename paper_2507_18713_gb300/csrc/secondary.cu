@@ -125,6 +125,7 @@ extern "C" salf_status salf_secondary_rays(salf_scene* sc, const salf_sensor* se
                                            const float* depth, const float* opacity,
                                            const salf_secondary_opts* so, float* rays_out,
                                            void* stream) {
+  SALF_RANGE("salf_secondary_rays");
   if (!sc || !sen || !depth || !opacity || !so || !rays_out) {
     salf_set_error("salf_secondary_rays: null argument");
     return SALF_ERR_INVALID;

@@ -265,6 +265,7 @@ void scheduler(salf_server* s) {
     if (inject) {
       bd->status = SALF_ERR_CUDA;
     } else {
+      SALF_RANGE("salf_serve_batch");  // one range per batched launch
       if (e == cudaSuccess) e = salf_launch_forward(*P, st);
       if (e != cudaSuccess) {
         cudaGetLastError();
