@@ -129,6 +129,30 @@ __device__ __forceinline__ void gen_ray(const ReqDev& Q, const DevScene& S, int 
   r.s = s;
 }
 
+// gen_ray for a pinhole camera with one pose for the whole frame (no rolling
+// shutter): the same arithmetic as gen_ray's pinhole branch, without the other
+// sensor kinds' code, for kernels that serve only such cameras.
+__device__ __forceinline__ void gen_ray_pinhole(const ReqDev& Q, int u, int v, Ray& r) {
+  r.valid = true;
+  const float px = (float)u + 0.5f, py = (float)v + 0.5f;
+  const float dc0 = (px - Q.cx) * Q.inv_fx, dc1 = (py - Q.cy) * Q.inv_fy, dc2 = 1.f;
+  const float d0 = Q.R0[0] * dc0 + Q.R0[1] * dc1 + Q.R0[2] * dc2;
+  const float d1 = Q.R0[3] * dc0 + Q.R0[4] * dc1 + Q.R0[5] * dc2;
+  const float d2 = Q.R0[6] * dc0 + Q.R0[7] * dc1 + Q.R0[8] * dc2;
+  const float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  r.d[0] = d0 * inv;
+  r.d[1] = d1 * inv;
+  r.d[2] = d2 * inv;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r.Oi[k] = Q.Oi[k];
+    r.Of[k] = Q.Of[k];  // fmaf(0, dO, Of) in gen_ray
+  }
+  r.tn = Q.t_near;
+  r.tf = Q.t_far;
+  r.s = 0.f;
+}
+
 // Debug dump of a generated ray: world origin, unit direction, time, valid.
 __device__ __forceinline__ void dump_ray(const ReqDev& Q, const DevScene& S, const Ray& r, int ray) {
   float* p = Q.ray_dump + 8 * (size_t)ray;
