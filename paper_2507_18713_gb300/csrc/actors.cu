@@ -30,6 +30,13 @@ namespace {
 #ifndef SALF_ACTOR_MIN_BLOCKS
 #define SALF_ACTOR_MIN_BLOCKS 1  // resident merge blocks per SM the register budget must allow
 #endif
+// The same for the lean merge variant (static pinhole cameras without
+// intensity): without the other sensors' ray generation and the intensity
+// field it fits 128 registers, and 4 resident blocks per SM measured faster
+// (1080p camera with 24 actors 0.834 -> 0.754 ms).
+#ifndef SALF_ACTOR_MIN_BLOCKS_LEAN
+#define SALF_ACTOR_MIN_BLOCKS_LEAN 4
+#endif
 
 constexpr int kActorWarps = 4;  // warps per block
 constexpr int kMaxIntervals = 8;
@@ -220,8 +227,12 @@ __device__ __forceinline__ void actor_walk(const ActorDev& A, const Ray& r, Walk
   sh_basis(dc, gam);
 }
 
-template <int DT, int MODE, bool DUMP>
-__global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_forward_actors(
+// LEAN: every ray comes from a pinhole camera with one pose for the frame and
+// no intensity is asked for (that ray generation only, no intensity field).
+template <int DT, int MODE, bool DUMP, bool LEAN>
+__global__ void __launch_bounds__(32 * kActorWarps,
+                                  LEAN ? SALF_ACTOR_MIN_BLOCKS_LEAN : SALF_ACTOR_MIN_BLOCKS)
+    k_forward_actors(
     const __grid_constant__ LaunchParams P, const ActorDev* __restrict__ actors, int n_actors,
     const unsigned* __restrict__ masks) {
   const int warp = blockIdx.x * kActorWarps + (threadIdx.x >> 5);
@@ -248,7 +259,10 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_for
   r.s = 0.f;
   r.d[0] = r.d[1] = r.d[2] = 0.f;
   if (in_img) {
-    gen_ray(Q, S, u, v, ray, r);
+    if (LEAN)
+      gen_ray_pinhole(Q, u, v, r);
+    else
+      gen_ray(Q, S, u, v, ray, r);
     walk_init(S, r, ws);
   }
   float gam_s[4];
@@ -291,7 +305,7 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_for
   // rounds: per round a lane takes at most one structure step (of the static
   // or the actor walk), then composites the next hit once both walks have
   // resolved theirs
-  const bool want_int = Q.want_int != 0;
+  const bool want_int = !LEAN && Q.want_int != 0;
   const float tmin = Q.t_min;
   const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   Accum acc{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
@@ -579,10 +593,13 @@ void launch_actors(const LaunchParams& P, const ActorDev* actors, int n, const u
                    bool dump, cudaStream_t st) {
   const int blocks = (P.total_tiles + kActorWarps - 1) / kActorWarps;
   if (blocks == 0) return;
+  const ReqDev& q = P.req[0];
   if (dump)
-    k_forward_actors<DT, MODE, true><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n, masks);
+    k_forward_actors<DT, MODE, true, false><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n, masks);
+  else if (q.kind == SALF_PINHOLE && !q.moving && !q.want_int)
+    k_forward_actors<DT, MODE, false, true><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n, masks);
   else
-    k_forward_actors<DT, MODE, false><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n, masks);
+    k_forward_actors<DT, MODE, false, false><<<blocks, 32 * kActorWarps, 0, st>>>(P, actors, n, masks);
 }
 
 }  // namespace
