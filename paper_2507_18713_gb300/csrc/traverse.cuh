@@ -708,7 +708,7 @@ __device__ __forceinline__ float composite_hit(const Walk& w, const Hit& h, cons
   A.C1 = fmaf(wgt, f.c[1], A.C1);
   A.C2 = fmaf(wgt, f.c[2], A.C2);
   A.Dp = fmaf(wgt, tm, A.Dp);
-  A.Ip = fmaf(wgt, f.io, A.Ip);
+  if (want_int) A.Ip = fmaf(wgt, f.io, A.Ip);
   if (want_drop) A.Rp = fmaf(wgt, f.dr, A.Rp);
   A.T *= e;
   return e;
