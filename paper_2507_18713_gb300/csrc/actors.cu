@@ -307,7 +307,6 @@ __global__ void __launch_bounds__(32 * kActorWarps,
   // resolved theirs
   const bool want_int = !LEAN && Q.want_int != 0;
   const float tmin = Q.t_min;
-  const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   Accum acc{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
   Hit hs, ha;
   bool hs_ok = false, ha_ok = false;
@@ -325,13 +324,13 @@ __global__ void __launch_bounds__(32 * kActorWarps,
     const bool start_next =
         cur < 0 && nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)));
     if (!hs_ok && ws.alive) {
-      hs_ok = next_hit(S, ws, hs, budget);
+      hs_ok = next_hit(S, ws, hs);
     } else if (start_next) {
       cur = iv_k[nxt++];
       actor_walk(actors[cur], r, wa, gam_a);
       ha_ok = false;
     } else if (cur >= 0 && !ha_ok && wa.alive) {
-      ha_ok = next_hit(actors[cur].S, wa, ha, budget);
+      ha_ok = next_hit(actors[cur].S, wa, ha);
     }
     // an actor walk that ended this round (or opened empty) leaves the next
     // interval to be weighed against the pending static hit
@@ -532,7 +531,6 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_bac
 
   // 2. the forward's merge walk, with the adjoint of each composited hit
   const bool want_int = Q.want_int != 0;
-  const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   float T = 1.f, Pk = 0.f;
   int done = 0;
   Hit hs, ha;
@@ -549,7 +547,7 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_bac
     const bool start_next =
         cur < 0 && nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)));
     if (!hs_ok && ws.alive) {
-      hs_ok = next_hit(S, ws, hs, budget);
+      hs_ok = next_hit(S, ws, hs);
     } else if (start_next) {
       cur = iv_k[nxt++];
       if (cur < 0 || cur >= n_actors) {  // never expected: record it and stop the ray
@@ -560,7 +558,7 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_bac
       actor_walk(actors[cur], r, wa, gam_a);
       ha_ok = false;
     } else if (cur >= 0 && !ha_ok && wa.alive) {
-      ha_ok = next_hit(actors[cur].S, wa, ha, budget);
+      ha_ok = next_hit(actors[cur].S, wa, ha);
     }
     // an actor walk that ended this round (or opened empty) leaves the next
     // interval to be weighed against the pending static hit

@@ -175,10 +175,9 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
     __syncwarp();
   };
 
-  const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   for (;;) {
     Hit h;
-    const bool hit = next_hit(S, w, h, budget);
+    const bool hit = next_hit(S, w, h);
     if (!__any_sync(0xffffffffu, hit || w.alive)) break;
     const unsigned hit_lanes = __ballot_sync(0xffffffffu, hit);
     if (hit) {

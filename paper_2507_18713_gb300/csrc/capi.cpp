@@ -266,15 +266,6 @@ void salf_relative_rotation(const double* pose0, const double* pose1, float axis
   for (int k = 0; k < 3; ++k) axis[k] = vn > 0 ? (float)(q[k + 1] / vn) : 0.f;
 }
 
-int salf_step_budget() {
-  static const int budget = [] {
-    const char* e = std::getenv("SALF_STEP_BUDGET");
-    const int v = e ? std::atoi(e) : 0;
-    return v > 0 ? v : 1;
-  }();
-  return budget;
-}
-
 // Tile row whose centre-column ray is closest to horizontal in the world
 // (launch-order heuristic only: near-horizontal rays are the longest in
 // driving scenes; it never changes a result).
@@ -488,7 +479,6 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
   if (st != SALF_OK) return st;
   if (out->ray_dump || out->steps || out->max_alpha) salf_request_tiling(&r, sen, 0);
   P.total_tiles = r.n_tiles;
-  P.step_budget = salf_step_budget();
   const size_t R = (size_t)salf_request_rays(sen);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
 
@@ -871,7 +861,6 @@ extern "C" salf_status salf_render_rays_actors(salf_scene* sc, const salf_actor*
   if (st != SALF_OK) return st;
   salf_request_tiling(&r, sen, 0);  // this path walks whole rays
   P.total_tiles = r.n_tiles;
-  P.step_budget = salf_step_budget();
   r.rgb = out->rgb;
   r.depth = out->depth;
   r.opacity = out->opacity;
@@ -1010,7 +999,6 @@ extern "C" salf_status salf_render_backward_actors(
   if (st != SALF_OK) return st;
   salf_request_tiling(&r, sen, 0);  // the forward's tiles (whole rays)
   P.total_tiles = r.n_tiles;
-  P.step_budget = salf_step_budget();
   r.vcap = 0;
   r.bsaved = saved;
   r.g_rgb = d_rgb;
@@ -1114,7 +1102,6 @@ extern "C" salf_status salf_render_rays_batch(salf_scene* sc, int32_t n,
     LaunchParams P;
     std::memset(&P, 0, sizeof(P));
     P.S = sc->dev;
-    P.step_budget = salf_step_budget();
     for (int i = b; i < std::min(n, b + SALF_MAX_BATCH); ++i) {
       ReqDev& r = P.req[P.n_req++];
       const salf_status st = salf_prepare_request(sc, &sensors[i], &o, &r);
@@ -1172,7 +1159,6 @@ extern "C" salf_status salf_render_backward_batch(
     LaunchParams P;
     std::memset(&P, 0, sizeof(P));
     P.S = sc->dev;
-    P.step_budget = salf_step_budget();
     for (int i = b; i < std::min(n, b + SALF_MAX_BATCH); ++i) {
       ReqDev& r = P.req[P.n_req++];
       const salf_status st = salf_prepare_request(sc, &sensors[i], &o, &r);
@@ -1243,7 +1229,6 @@ extern "C" salf_status salf_render_backward(salf_scene* sc, const salf_sensor* s
   r.g_raydrop = d_raydrop;
   r.d_params = d_params;
   P.total_tiles = r.n_tiles;
-  P.step_budget = salf_step_budget();
   if ((e = salf_launch_backward(P, static_cast<cudaStream_t>(stream))) != cudaSuccess)
     return salf_cuda_fail(e, "backward launch");
   return SALF_OK;

@@ -109,7 +109,6 @@ extern "C" salf_status salf_render_rays_host_noalloc(salf_scene* sc, const salf_
     }
   }
   P.total_tiles = r.n_tiles;
-  P.step_budget = salf_step_budget();
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   // page-locked, device-addressable host outputs: the kernel writes them in
   // place (no staging, no copy step)

@@ -6,8 +6,8 @@
 // density and Eq. 2 colour at each segment midpoint -> Eq. 3-4 front-to-back
 // compositing, stopping once the transmittance drops below t_min.
 //
-// Each round of the loop, every live lane takes at most `step_budget`
-// structure steps toward its next hit voxel (empty leaves are skipped whole),
+// Each round of the loop, every live lane takes one structure step toward its
+// next hit voxel (empty leaves are skipped whole),
 // then the lanes that have a hit gather their records and composite together;
 // the warp leaves the loop when no lane has work left (ballot).  Lanes whose
 // ray terminated early idle in the ballot.
@@ -127,11 +127,10 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   float T_prev = 1.f;  // SEG: this span's T before its last composited hit
   bool keep = true;    // SEG: the whole ray reaches this lane's span
 
-  const int budget = P.step_budget > 0 ? P.step_budget : 1 << 30;
   for (int pass = 0;; ++pass) {
     for (;;) {
       Hit h;
-      bool hit = next_hit(S, w, h, budget);
+      bool hit = next_hit(S, w, h);
       if (SEG && !hit && w.t > walk_end) w.alive = false;  // the rest is the next span's
       if (!__any_sync(0xffffffffu, hit || w.alive)) break;
       if (SEG && hit && ks > 0) {  // composite only the voxels entered inside this span

@@ -171,7 +171,6 @@ struct LaunchParams {
   DevScene S;
   int n_req;
   int total_tiles;
-  int step_budget;  // structure steps per lane between warp-wide compositing rounds
   ReqDev req[SALF_MAX_BATCH];
 };
 
@@ -270,9 +269,6 @@ int salf_auto_segments(int kind);
 int64_t salf_request_rays(const salf_sensor* sen);
 void salf_relative_rotation(const double* pose0, const double* pose1, float axis[3],
                             float* angle);
-// Structure steps per lane between warp-wide compositing rounds (environment
-// override SALF_STEP_BUDGET, read once).
-int salf_step_budget();
 cudaError_t salf_launch_gather_params(const float* in, const int* order, void* out, int64_t n,
                                       int dtype, int mode, int* status, cudaStream_t st);
 cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st);

@@ -247,7 +247,6 @@ void scheduler(salf_server* s) {
       s->rays += r.rays;
     }
     P->total_tiles = tiles;
-    P->step_budget = salf_step_budget();
     s->stream_busy[idle]++;
     s->launches++;
     s->requests_launched += (int64_t)batch.size();

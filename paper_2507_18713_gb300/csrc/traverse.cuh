@@ -409,15 +409,16 @@ __device__ __forceinline__ void hop(const DevScene& S, Walk& w, const int lo[3],
   w.t = fmaxf(w.t, te);
 }
 
-// Advance `w` toward the next voxel crossed with positive length, taking at
-// most `budget` structure steps (the caller's warp composites the lanes that
-// found one, then calls again: a small budget keeps lanes of different rays in
-// step, so a warp costs about its heaviest ray, not the sum of per-round
-// maxima).  Empty space is left through the farther of two empty boxes around
-// the current cell: the largest empty aligned pyramid cell, and the column-
-// pyramid skip.
-__device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int budget) {
-  for (int it = 0; it < budget && w.alive; ++it) {
+// Advance `w` by one structure step toward the next voxel crossed with
+// positive length; true if this step found it (in h).  The caller's warp
+// composites the lanes that found one, then calls again: one step per call
+// keeps lanes of different rays in step, so a warp costs about its heaviest
+// ray, not the sum of per-round maxima (two or three steps per call measured
+// slower, and the loop for them cost 1-3% even when it ran once).  Empty space
+// is left through the farther of two empty boxes around the current cell: the
+// largest empty aligned pyramid cell, and the column-pyramid skip.
+__device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h) {
+  if (w.alive) {
     // the column mask depends only on the cell: issue its load with the pyramid's
     const int cl = w.cl;
 #if SALF_COL_EARLY
@@ -484,7 +485,7 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h, int
     }
     // one hop for every lane, whichever box it leaves (keeps the warp converged)
     hop(S, w, lo, hi, ax, te);
-    if (found) return true;
+    return found;
   }
   return false;
 }
@@ -530,7 +531,7 @@ struct Record<SALF_BF16> {
 // [base, base + 2^ls) (finest cells): x = (p - centre) / (edge / 2).
 __device__ __forceinline__ void local_coords(const Walk& w, const Hit& h, float tm, float x[3]) {
   const float E = (float)(1 << h.ls);
-  const float inv_half = 2.f / E;
+  const float inv_half = __int_as_float((128 - h.ls) << 23);  // 2 / E, exact: E = 2^ls
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float p = fmaf(tm, w.D[a], w.Of[a]);  // relative to the origin cell
