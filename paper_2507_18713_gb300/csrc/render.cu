@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_forward(const __grid_constan
   for (int pass = 0;; ++pass) {
     for (;;) {
       Hit h;
-      bool hit = next_hit(S, w, h);
+      bool hit = next_hit<!SEG>(S, w, h);
       if (SEG && !hit && w.t > walk_end) w.alive = false;  // the rest is the next span's
       if (!__any_sync(0xffffffffu, hit || w.alive)) break;
       if (SEG && hit && ks > 0) {  // composite only the voxels entered inside this span

@@ -401,7 +401,7 @@ __device__ __forceinline__ void hop(const DevScene& S, Walk& w, const int lo[3],
     } else {
       int q = w.Oi[a] + __float2int_rd(fmaf(te, w.D[a], w.Of[a]));
       q = min(max(q, lo[a]), hi[a] - 1);
-      q = min(max(q, 0), S.Gf[a] - 1);
+      q = min(q, S.Gf[a] - 1);  // boxes start at >= 0, so q >= 0 already
       w.c[a] = w.D[a] > 0.f ? max(q, w.c[a]) : min(q, w.c[a]);
     }
   }
@@ -417,6 +417,12 @@ __device__ __forceinline__ void hop(const DevScene& S, Walk& w, const int lo[3],
 // slower, and the loop for them cost 1-3% even when it ran once).  Empty space
 // is left through the farther of two empty boxes around the current cell: the
 // largest empty aligned pyramid cell, and the column-pyramid skip.
+// FMIN: take the exit distance as the minimum of the three plane distances
+// (the same value as indexing them by the exit axis, as they are finite); the
+// indexed form keeps the array in local memory, the minimum does not.  The
+// span-parallel kernel measured 1.3% slower with it, so it keeps the indexed
+// form.
+template <bool FMIN = true>
 __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h) {
   if (w.alive) {
     // the column mask depends only on the cell: issue its load with the pyramid's
@@ -437,7 +443,7 @@ __device__ __forceinline__ bool next_hit(const DevScene& S, Walk& w, Hit& h) {
       tx[a] = ((float)p - w.Of[a]) * w.invD[a];
     }
     int ax = (tx[0] <= tx[1] && tx[0] <= tx[2]) ? 0 : (tx[1] <= tx[2] ? 1 : 2);
-    float te = tx[ax];
+    float te = FMIN ? fminf(fminf(tx[0], tx[1]), tx[2]) : tx[ax];
     bool found = false;
     if (vox >= 0) {
       float tin = w.t;
