@@ -31,11 +31,14 @@ namespace {
 #define SALF_ACTOR_MIN_BLOCKS 1  // resident merge blocks per SM the register budget must allow
 #endif
 // The same for the lean merge variant (static pinhole cameras without
-// intensity): without the other sensors' ray generation and the intensity
-// field it fits 128 registers, and 4 resident blocks per SM measured faster
-// (1080p camera with 24 actors 0.834 -> 0.754 ms).
+// intensity).  Without the other sensors' ray generation and the intensity
+// field it fits 128 registers: 4 resident blocks per SM measured faster (1080p
+// camera with 24 actors 0.834 -> 0.754 ms).  5 blocks (96 registers, 64 bytes
+// of spills) were faster again (0.717 -> 0.689 ms), and 6 no better.  Merge
+// blocks hold most of an SM's registers while they run, so the ray kernel
+// beside them gets few slots; the merge kernel's total warp time sets the frame.
 #ifndef SALF_ACTOR_MIN_BLOCKS_LEAN
-#define SALF_ACTOR_MIN_BLOCKS_LEAN 4
+#define SALF_ACTOR_MIN_BLOCKS_LEAN 5
 #endif
 
 constexpr int kActorWarps = 4;  // warps per block
