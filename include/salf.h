@@ -17,7 +17,7 @@
  *     (a cudaStream_t passed as void*; NULL = the legacy default stream),
  *     unless the outputs are host memory (salf_outputs.on_host = 1), in which
  *     case the call also copies the results back and returns after the stream
- *     has drained.
+ *     has drained (on_host = 2: page-locked host outputs, asynchronous).
  *   - Output buffers are owned by the caller.  Contexts, scenes and servers
  *     are owned by the library (created/destroyed through this API).
  *   - World frame: metres, right-handed, z up.  Camera frame: x right, y down,
@@ -191,6 +191,12 @@ typedef struct {
  * address (cudaHostAlloc / cudaHostRegister under unified addressing; saved
  * 16-byte aligned) are written by the kernel in place; otherwise the library
  * renders into its own device staging buffers and copies back.
+ * on_host = 2 (salf_render_rays only): page-locked host pointers the device
+ * can address, written by the kernel in place, and the call is asynchronous
+ * like a device-output render: the buffers hold the results once `stream`
+ * has drained (cudaStreamSynchronize, or an event recorded after the call).
+ * A caller can so keep several frames in flight, each in its own buffers.
+ * Any other host buffer is rejected (SALF_ERR_INVALID); nothing is staged.
  */
 typedef struct {
   float* rgb;

@@ -488,9 +488,11 @@ class Scene:
 
     def render_host(self, sensor: dict, t_min=1e-4, background=(0.0, 0.0, 0.0),
                     want_intensity=False, outputs=("rgb", "depth", "opacity"), out=None,
-                    stream=None, ray_segments: int = 0) -> dict:
+                    stream=None, ray_segments: int = 0, sync: bool = True) -> dict:
         """salf_render_rays with host output buffers (on_host = 1): synchronous,
-        results land in (pinned, if given) host memory."""
+        results land in (pinned, if given) host memory.  sync=False (on_host = 2):
+        `out` must be pinned; the call returns after the launch and the buffers
+        hold the results once `stream` has drained."""
         R = n_rays(sensor)
         shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,),
                   "raydrop": (R,)}
@@ -499,7 +501,7 @@ class Scene:
         o = L.Outputs()
         for k, v in res.items():
             setattr(o, k, v.data_ptr())
-        o.on_host = 1
+        o.on_host = 1 if sync else 2
         keep: list = []
         s = sensor_struct(sensor, keep)
         op = opts_struct(t_min, background, want_intensity, 0, ray_segments)

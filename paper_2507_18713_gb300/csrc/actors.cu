@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(32 * kActorWarps,
   wa.alive = false;
   float gam_a[4] = {0.f, 0.f, 0.f, 0.f};
   int cur = -1, nxt = 0;
+  float nxt_in = ni > 0 ? iv_in[0] : 0.f;  // entry of interval nxt (the list is in local memory)
   bool live = in_img && r.valid;
   for (;;) {
     if (!__any_sync(0xffffffffu, live)) break;
@@ -325,11 +326,12 @@ __global__ void __launch_bounds__(32 * kActorWarps,
     // the next actor box starts before the pending static hit (a little early
     // is harmless: hits are composited by entry)
     const bool start_next =
-        cur < 0 && nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)));
+        cur < 0 && nxt < ni && (!hs_ok || nxt_in <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)));
     if (!hs_ok && ws.alive) {
       hs_ok = next_hit(S, ws, hs);
     } else if (start_next) {
       cur = iv_k[nxt++];
+      nxt_in = nxt < ni ? iv_in[nxt] : 0.f;
       actor_walk(actors[cur], r, wa, gam_a);
       ha_ok = false;
     } else if (cur >= 0 && !ha_ok && wa.alive) {
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(32 * kActorWarps,
     // interval to be weighed against the pending static hit
     if (cur >= 0 && !ha_ok && !wa.alive) cur = -1;
     const bool s_res = hs_ok || !ws.alive;
-    const bool a_res = cur < 0 ? !(nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin))))
+    const bool a_res = cur < 0 ? !(nxt < ni && (!hs_ok || nxt_in <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin))))
                                : (ha_ok || !wa.alive);
     if (!(s_res && a_res)) continue;
     if (ha_ok && (!hs_ok || ha.tin < hs.tin)) {
@@ -542,17 +544,19 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_bac
   wa.alive = false;
   float gam_a[4] = {0.f, 0.f, 0.f, 0.f};
   int cur = -1, nxt = 0;
+  float nxt_in = ni > 0 ? iv_in[0] : 0.f;  // entry of interval nxt (the list is in local memory)
   bool live = in_img && r.valid && nv > 0;
   for (;;) {
     if (!__any_sync(0xffffffffu, live)) break;
     if (!live) continue;
     if (cur >= 0 && !ha_ok && !wa.alive) cur = -1;
     const bool start_next =
-        cur < 0 && nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)));
+        cur < 0 && nxt < ni && (!hs_ok || nxt_in <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin)));
     if (!hs_ok && ws.alive) {
       hs_ok = next_hit(S, ws, hs);
     } else if (start_next) {
       cur = iv_k[nxt++];
+      nxt_in = nxt < ni ? iv_in[nxt] : 0.f;
       if (cur < 0 || cur >= n_actors) {  // never expected: record it and stop the ray
         atomicOr(S.status, SALF_DEVERR_BOUNDS);
         live = false;
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(32 * kActorWarps, SALF_ACTOR_MIN_BLOCKS) k_bac
     // interval to be weighed against the pending static hit
     if (cur >= 0 && !ha_ok && !wa.alive) cur = -1;
     const bool s_res = hs_ok || !ws.alive;
-    const bool a_res = cur < 0 ? !(nxt < ni && (!hs_ok || iv_in[nxt] <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin))))
+    const bool a_res = cur < 0 ? !(nxt < ni && (!hs_ok || nxt_in <= hs.tin + 1e-5f * fmaxf(1.f, fabsf(hs.tin))))
                                : (ha_ok || !wa.alive);
     if (!(s_res && a_res)) continue;
     if (ha_ok && (!hs_ok || ha.tin < hs.tin)) {

@@ -460,6 +460,10 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
     g_err = "salf_render_rays: visits_cap > 0 needs visits and visit_count";
     return SALF_ERR_INVALID;
   }
+  if (out->on_host < 0 || out->on_host > 2) {
+    g_err = "salf_render_rays: on_host must be 0, 1 or 2";
+    return SALF_ERR_INVALID;
+  }
   if (out->on_host && (out->ray_dump || out->steps || out->max_alpha)) {
     g_err = "salf_render_rays: ray_dump, steps and max_alpha need device outputs";
     return SALF_ERR_INVALID;
@@ -550,8 +554,14 @@ extern "C" salf_status salf_render_rays(salf_scene* sc, const salf_sensor* sen,
       r.raydrop = static_cast<float*>(dp[8]);
       if ((e = salf_launch_forward(P, cs)) != cudaSuccess)
         return salf_cuda_fail(e, "forward launch");
+      if (out->on_host == 2) return SALF_OK;  // asynchronous: results once the stream drains
       if ((e = cudaStreamSynchronize(cs)) != cudaSuccess) return salf_cuda_fail(e, "render");
       return SALF_OK;
+    }
+    if (out->on_host == 2) {
+      g_err = "salf_render_rays: on_host = 2 needs page-locked host buffers the device can "
+              "address (saved 16-byte aligned; explicit rays in device or page-locked memory)";
+      return SALF_ERR_INVALID;
     }
     r.rays = sen->rays;
   }

@@ -285,6 +285,37 @@ def test_pinned_host_outputs_are_written_in_place(salf):
     g.check()
 
 
+def test_async_pinned_host_outputs(salf):
+    """on_host = 2: page-locked outputs written in place, the call returns after
+    the launch; two frames in flight in their own buffers equal the device
+    renders bit for bit once the stream drains.  Pageable buffers are refused."""
+    sc = synth.random_multilevel_scene(seed=7, max_level=2, dims=(6, 5, 4), p_occ=0.7)
+    g = salf.Scene(sc)
+    outs = ("rgb", "depth", "opacity")
+    cams = [synth.pinhole(320, 240, 75.0, synth.camera_pose_looking((-2.2, 0.6 + 0.2 * i, 1.1),
+                                                                     0.15)) for i in range(2)]
+    refs = []
+    for cam in cams:
+        d = g.render(cam, outputs=outs)
+        torch.cuda.synchronize()
+        refs.append({k: d[k].cpu() for k in outs})
+    bufs = [{k: torch.empty_like(v).pin_memory() for k, v in ref.items()} for ref in refs]
+    for b in bufs:
+        for v in b.values():
+            v.fill_(-7.0)
+    st = torch.cuda.Stream()
+    for cam, b in zip(cams, bufs):  # both frames in flight before any wait
+        g.render_host(cam, outputs=outs, out=b, sync=False, stream=st)
+    st.synchronize()
+    for ref, b in zip(refs, bufs):
+        for k in outs:
+            assert torch.equal(ref[k], b[k]), k
+    with pytest.raises(salf.SalfError):
+        g.render_host(cams[0], outputs=outs, out={k: torch.empty_like(v) for k, v in refs[0].items()},
+                      sync=False)
+    g.check()
+
+
 def test_update_params_matches_rebuild(salf):
     sc = synth.random_multilevel_scene(seed=2, max_level=2)
     sen = synth.pinhole(40, 30, 75.0, synth.camera_pose_looking((-2.2, 0.6, 1.1), 0.15))
