@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kRasterThreads, SALF_RASTER_MIN_BLOCKS) k_rast
   r.valid = false;
   r.d[0] = r.d[1] = r.d[2] = 0.f;
   if (in_img) {
-    gen_ray(Q, S, u, v, ray, r);
+    gen_ray_pinhole(Q, u, v, r);  // the rasteriser serves pinhole cameras with one pose
     walk_init(S, r, w);
   }
   float gam[4];
@@ -298,9 +298,10 @@ __global__ void __launch_bounds__(kRasterThreads, SALF_RASTER_MIN_BLOCKS) k_rast
         tx[a] = pe * w.invD[a];
         tin = fmaxf(tin, pn * w.invD[a]);
       }
-      const int ax = (tx[0] <= tx[1] && tx[0] <= tx[2]) ? 0 : (tx[1] <= tx[2] ? 1 : 2);
+      // the exit is the nearest exit plane (the ray kernel's tx[ax]: the same value, as the
+      // distances are finite), taken as a minimum so the distances stay in registers
       *tin_out = tin;
-      *tout_out = fminf(tx[ax], w.tend);
+      *tout_out = fminf(fminf(fminf(tx[0], tx[1]), tx[2]), w.tend);
     };
     // phase 1: which of the strip's voxels this pixel's ray crosses
     unsigned hits[kChunk / 32];
