@@ -633,11 +633,25 @@ def main():
     achieved = bytes_alg / (avg * 1e-3) / 1e9
     traffic = None
     inst = None
+    l2_bytes = None
     try:
         ent = json.load(open(TRAFFIC_FILE)).get(args.workload, {})
         if ent.get("kernel_hash") == kernel_hash(args.workload):
             traffic = ent.get("dram_bytes_per_launch")
             inst = ent.get("warp_inst_per_launch")
+            l2_bytes = ent.get("l2_bytes_per_launch")
+    except Exception:
+        pass
+    # L2 read bandwidth of this GPU (streaming reads of a 96 MiB buffer resident in L2; smaller
+    # buffers give each thread too few loads per pass to reach it): the kernels take most of
+    # their bytes from L1 and L2, so their L2 traffic is set against it
+    l2_peak = None
+    try:
+        from paper_2507_18713_gb300 import _lib as _L2
+        import ctypes as _C
+        _g = _C.c_double(0.0)
+        if _L2.load().salf_measure_l2_read(local, 96 << 20, 20, _C.byref(_g)) == 0:
+            l2_peak = _g.value
     except Exception:
         pass
     # issue fraction: warp instructions of the launch (ncu smsp__inst_executed.sum)
@@ -743,7 +757,16 @@ def main():
                               kernel="k_raster<F32,EXP> (whole pipeline timed)" if raster
                               else "k_forward<F32,EXP>",
                               note="bytes = visits x record scalars read + outputs per ray; "
-                                   "visits counted by the kernel"),
+                                   "visits counted by the kernel",
+                              l2=dict(peak_gbs=l2_peak,
+                                      bytes_per_launch=l2_bytes,
+                                      achieved_gbs=(l2_bytes / (avg * 1e-3) / 1e9
+                                                    if l2_bytes else None),
+                                      frac=(l2_bytes / (avg * 1e-3) / 1e9 / l2_peak
+                                            if l2_bytes and l2_peak else None),
+                                      note="L2 traffic of the launch (ncu lts__t_sectors.sum x "
+                                           "32 B, from the profile of these kernel sources) "
+                                           "against the L2 read bandwidth measured here")),
                 e2e=dict(value=e2e_value, unit="Mrays/s", sync_value=e2e_sync_value,
                          inplace_pipelined_value=None if raster else e2e_inplace_value,
                          h2d_bytes_per_step=param_bytes,

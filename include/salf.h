@@ -628,6 +628,14 @@ void salf_serve_destroy(salf_server* srv);
  * so this is all a device-output render sends to the GPU. */
 size_t salf_launch_param_bytes(void);
 
+/* Measurement utility, not part of the method: the read bandwidth of this
+ * GPU's L2 in GB/s, from `reps` streaming reads of a `bytes`-long device buffer
+ * that the call allocates, fills and frees (bytes in [1 MiB, 4 GiB]; a buffer
+ * smaller than L2 stays resident after the warm-up reads).  The render kernels
+ * take most of their record and structure bytes from L1 and L2, so their L2
+ * traffic is reported against this figure.  Synchronous.  Errors: INVALID, CUDA. */
+salf_status salf_measure_l2_read(int32_t device, int64_t bytes, int32_t reps, double* gbs);
+
 /* Thread-local message of the last failing call on this thread. */
 const char* salf_last_error(void);
 

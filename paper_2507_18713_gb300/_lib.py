@@ -139,6 +139,7 @@ SIGNATURES = {
     "salf_serve_hold": ([c_void_p, c_int32], c_int32),
     "salf_serve_destroy": ([c_void_p], None),
     "salf_launch_param_bytes": ([], C.c_size_t),
+    "salf_measure_l2_read": ([C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_double)], C.c_int),
     "salf_last_error": ([], C.c_char_p),
 }
 

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["render.cu", "backward.cu", "params.cu", "noalloc.cu", "raster.cu", "actors.cu",
-                "refine.cu", "scene_build_gpu.cu", "secondary.cu"]
+                "refine.cu", "scene_build_gpu.cu", "secondary.cu", "measure.cu"]
 CXX_SOURCES = ["capi.cpp", "scene_build.cpp", "serve.cpp", "checkpoint.cpp"]
 HEADERS = ["salf_internal.h", "traverse.cuh", "scan.cuh", "sort.cuh"]
 
