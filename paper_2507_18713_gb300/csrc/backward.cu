@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
       const float* it = queue + ((head + lane) & (QN - 1)) * QW;
       key = __float_as_int(it[0]);
       const float xh[4] = {it[1], it[2], it[3], 1.f};
-      const float gm[4] = {it[12], it[13], it[14], it[15]};
+      const float gm[4] = {kSH0, it[13], it[14], it[15]};  // gamma_0 is a constant
 #pragma unroll
       for (int q = 0; q < 4; ++q) gr[q] = it[4] * xh[q];
 #pragma unroll
@@ -133,11 +133,12 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
 #pragma unroll
         for (int b = 0; b < 4; ++b) gr[13 + 4 * ch + b] = dz * gm[b];
       }
-      gr[25] = it[5];
-      gr[26] = it[6];
+      gr[25] = MODE == SALF_FIELD_EXP ? 0.f : it[5];  // SDF a, b (not queued in EXP mode)
+      gr[26] = MODE == SALF_FIELD_EXP ? 0.f : it[6];
+      const float di = want_int ? it[10] : 0.f, dr = want_drop ? it[11] : 0.f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) gr[27 + q] = it[10] * xh[q];
-      gr[31] = it[11];
+      for (int q = 0; q < 4; ++q) gr[27 + q] = di * xh[q];
+      gr[31] = dr;
     }
     __syncwarp();
     const unsigned act_lanes = __ballot_sync(0xffffffffu, act);
@@ -191,8 +192,11 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
       const float* c = f.c;
       const float e = __expf(-sig * dl);
       const float wgt = T * (1.f - e);
-      const float gq =
-          g[0] * c[0] + g[1] * c[1] + g[2] * c[2] + g[3] * tm + g[4] + g[5] * io + gp * f.dr;
+      // the intensity and raydrop terms only when asked for (a product with a zero
+      // factor is not dropped by the compiler)
+      float gq = g[0] * c[0] + g[1] * c[1] + g[2] * c[2] + g[3] * tm + g[4];
+      if (want_int) gq += g[5] * io;
+      if (want_drop) gq += gp * f.dr;
       Pk = fmaf(wgt, gq, Pk);
       const float Tn = T * e;
       const float dtau = Tn * gq - (gQ - Pk) - Tend * gbg;
@@ -205,8 +209,6 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
       it[3] = x[2];
       if (MODE == SALF_FIELD_EXP) {
         it[4] = dsig * sig;
-        it[5] = 0.f;
-        it[6] = 0.f;
       } else {
         const float a = f.a, b = f.b;
         const float ex = __expf(-fabsf(lin) / b);
@@ -216,9 +218,8 @@ __global__ void __launch_bounds__(32 * SALF_BWD_WARPS, SALF_BWD_MIN_BLOCKS)
       }
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) it[7 + ch] = wgt * g[ch] * c[ch] * (1.f - c[ch]);
-      it[10] = want_int ? wgt * g[5] * io * (1.f - io) : 0.f;
-      it[11] = want_drop ? wgt * gp * f.dr * (1.f - f.dr) : 0.f;
-      it[12] = gam[0];
+      if (want_int) it[10] = wgt * g[5] * io * (1.f - io);
+      if (want_drop) it[11] = wgt * gp * f.dr * (1.f - f.dr);
       it[13] = gam[1];
       it[14] = gam[2];
       it[15] = gam[3];
