@@ -275,19 +275,30 @@ static cudaError_t launch_variant(const LaunchParams& P, cudaStream_t st) {
   return launch_fm<SALF_BF16, SALF_FIELD_SDF>(P, dump, coherent, seg, rd, want_int, pinhole, st);
 }
 
-// A batch that mixes span-parallel requests with whole-ray ones runs as two
-// launches (one per variant), so the whole-ray requests keep their own
-// variant's shape; each request's result does not depend on the split.
+// A batch that mixes requests of different variants runs as one launch per
+// variant: span-parallel requests; static pinhole cameras that ask for no
+// intensity or raydrop (the lean variant); the rest.  Each group keeps its own
+// variant's code and shape, and each request's result does not depend on the
+// split (the lean variant's outputs equal the general one's bit for bit).
+static int variant_group(const ReqDev& q) {
+  if (q.seg_shift > 0) return 0;
+  const bool dump = q.vcap > 0 || q.ray_dump || q.steps_out || q.max_alpha;
+  if (q.kind == SALF_PINHOLE && !q.moving && !q.want_int && !q.raydrop && !dump) return 1;
+  return 2;
+}
+
 cudaError_t salf_launch_forward(const LaunchParams& P, cudaStream_t st) {
-  int n_seg = 0;
-  for (int i = 0; i < P.n_req; ++i) n_seg += P.req[i].seg_shift > 0;
-  if (n_seg == 0 || n_seg == P.n_req || P.req[0].tile_list) return launch_variant(P, st);
-  for (int part = 0; part < 2; ++part) {
+  int count[3] = {0, 0, 0};
+  for (int i = 0; i < P.n_req; ++i) ++count[variant_group(P.req[i])];
+  const int groups = (count[0] > 0) + (count[1] > 0) + (count[2] > 0);
+  if (groups <= 1 || P.req[0].tile_list) return launch_variant(P, st);
+  for (int part = 0; part < 3; ++part) {
+    if (!count[part]) continue;
     LaunchParams G = P;
     G.n_req = 0;
     G.total_tiles = 0;
     for (int i = 0; i < P.n_req; ++i) {
-      if ((P.req[i].seg_shift > 0) != (part == 0)) continue;
+      if (variant_group(P.req[i]) != part) continue;
       G.req[G.n_req] = P.req[i];
       G.req[G.n_req].tile_begin = G.total_tiles;
       G.total_tiles += P.req[i].n_tiles;

@@ -293,6 +293,37 @@ def test_training_config_finite_differences(salf, oracle_lib):
     print("FD check:", stats, "rays left out", n_left_out, "of", 8 * 1024)
 
 
+def test_batched_render_split_by_variant_equals_per_sensor_calls(salf):
+    """A batch without intensity runs one launch per kernel variant: the static
+    pinholes (lean variant), the LiDAR (spans) and the rest (fisheye, explicit
+    rays, a rolling-shutter pinhole).  Every sensor's outputs equal its own
+    call's bit for bit."""
+    sc = synth.random_multilevel_scene(seed=9, max_level=2, dims=(6, 5, 4), p_occ=0.7)
+    g = salf.Scene(sc)
+    rng = np.random.default_rng(6)
+    o = np.array([-2.0, 0.6, 1.0])
+    d = rng.normal(size=(200, 3)) * 0.3 + np.array([1.0, 0.0, 0.0])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.concatenate([np.tile(o, (200, 1)), d, np.zeros((200, 2))], axis=1)
+    sensors = [synth.pinhole(64, 48, 70.0, synth.camera_pose_looking((-2.1, 0.5, 1.05), 0.2)),
+               synth.fisheye(48, 40, 190.0, synth.camera_pose_looking((-2.0, 0.7, 1.1), 0.3)),
+               synth.lidar(16, 128, synth.lidar_pose((0.3, 0.5, 1.0), 0.1),
+                           synth.lidar_pose((0.6, 0.6, 1.0), 0.2), t0=0, t1=0.1),
+               synth.explicit_rays(rays),
+               synth.pinhole(40, 30, 75.0, synth.camera_pose_looking((-2.2, 0.3, 1.2), -0.1)),
+               synth.pinhole(40, 30, 75.0, synth.camera_pose_looking((-2.2, 0.3, 1.2), -0.1),
+                             synth.camera_pose_looking((-2.1, 0.35, 1.2), -0.05), t0=0.0, t1=0.03,
+                             rolling_shutter=True)]
+    outs = ("rgb", "depth", "opacity")
+    batch = g.render_batch(sensors, outputs=outs, saved=True, t_min=1e-3)
+    lone = [g.render(s, outputs=outs, saved=True, t_min=1e-3) for s in sensors]
+    torch.cuda.synchronize()
+    for b, l, s in zip(batch, lone, sensors):
+        for k in outs + ("saved", "valid"):
+            assert torch.equal(b[k], l[k]), (s["kind"], k)
+    g.check()
+
+
 def test_batched_render_and_adjoint_equal_per_sensor_calls(salf):
     """salf_render_rays_batch gives each sensor the outputs of its own call bit
     for bit (pinhole, fisheye, LiDAR spans and explicit rays in one batch);
