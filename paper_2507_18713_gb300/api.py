@@ -496,8 +496,8 @@ class Scene:
         R = n_rays(sensor)
         shapes = {"rgb": (R, 3), "depth": (R,), "opacity": (R,), "intensity": (R,),
                   "raydrop": (R,)}
-        res = out if out is not None else {k: torch.empty(shapes[k], dtype=torch.float32)
-                                           for k in outputs}
+        res = out if out is not None else {
+            k: torch.empty(shapes[k], dtype=torch.float32, pin_memory=not sync) for k in outputs}
         o = L.Outputs()
         for k, v in res.items():
             setattr(o, k, v.data_ptr())
