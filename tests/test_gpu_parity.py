@@ -313,6 +313,15 @@ def test_async_pinned_host_outputs(salf):
     with pytest.raises(salf.SalfError):
         g.render_host(cams[0], outputs=outs, out={k: torch.empty_like(v) for k, v in refs[0].items()},
                       sync=False)
+    # on_host outside 0..2 is refused before any work
+    from paper_2507_18713_gb300.api import opts_struct, sensor_struct
+    o = salf._lib.Outputs()
+    o.depth = bufs[0]["depth"].data_ptr()
+    o.on_host = 3
+    keep: list = []
+    s = sensor_struct(cams[0], keep)
+    op = opts_struct(1e-4, (0.0, 0.0, 0.0), False, 0)
+    assert salf._lib.load().salf_render_rays(g._h, C.byref(s), C.byref(op), C.byref(o), None) != 0
     g.check()
 
 
