@@ -677,11 +677,11 @@ def main():
     else:
         def e2e_call():
             g.render_host(cam, out=host, want_intensity=want_int)
-        e2e_how = ("salf_render_rays into device buffers on one stream, each frame's outputs "
-                   "copied into page-locked host buffers by the copy engine on a second stream "
-                   "while the next frame renders (two frames in flight, each in its own "
-                   "buffers); every frame's results are in host memory, and waited for, inside "
-                   "the timed region")
+        e2e_how = ("HostFrames: salf_render_rays into device buffers on one stream, each "
+                   "frame's outputs copied into page-locked host buffers by the copy engine on "
+                   "a second stream while the next frame renders (two frames in flight, each in "
+                   "its own buffers); every frame's results are in host memory, and waited for, "
+                   "inside the timed region")
     e2e_steps = max(10, args.steps // 4)
     # synchronous calls, one frame at a time
     for _ in range(args.warmup):
@@ -715,28 +715,17 @@ def main():
         e2e_frames(e2e_steps)
         e2e_inplace_value = world * n_counted * e2e_steps / (time.perf_counter() - t0) / 1e6
 
-        # device outputs + copy engine: frame i renders on st while frame i - 1 copies on cst
-        cst = torch.cuda.Stream()
-        dsets = (out, {k: torch.empty_like(v) for k, v in out.items()})
-        r_done = (torch.cuda.Event(), torch.cuda.Event())
-        c_done = (torch.cuda.Event(), torch.cuda.Event())
+        # device outputs + copy engine (HostFrames): frame i renders while frame i - 1 copies
+        frames = P.HostFrames(g, cam, outputs=outs, depth=2, want_intensity=want_int)
 
         def e2e_copy_frames(n):
-            for i in range(n):
-                b = i & 1
-                if i >= 2:
-                    st.wait_event(c_done[b])  # frame i - 2's copy has read dsets[b]
-                g.render(cam, out=dsets[b], outputs=outs, valid=False, want_intensity=want_int,
-                         stream=st)
-                r_done[b].record(st)
-                cst.wait_event(r_done[b])
-                with torch.cuda.stream(cst):
-                    for k in outs:
-                        sets[b][k].copy_(dsets[b][k], non_blocking=True)
-                c_done[b].record(cst)
-                if i >= 1:
-                    c_done[(i - 1) & 1].synchronize()  # frame i - 1 is in host memory
-            c_done[(n - 1) & 1].synchronize()
+            prev = None
+            for _ in range(n):
+                slot = frames.submit(cam)
+                if prev is not None:
+                    frames.result(prev)  # frame i - 1 is in host memory
+                prev = slot
+            frames.result(prev)
 
         e2e_copy_frames(max(2, args.warmup))
         t0 = time.perf_counter()

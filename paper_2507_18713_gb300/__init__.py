@@ -5,5 +5,5 @@ ABI of include/salf.h); this package is the thin Python binding.
 """
 
 from ._lib import SalfError, library_path, load  # noqa: F401
-from .api import (Context, RenderBatchFn, RenderFn, Scene, Server, VoxelSet,  # noqa: F401
+from .api import (Context, HostFrames, RenderBatchFn, RenderFn, Scene, Server, VoxelSet,  # noqa: F401
                   device_view, n_rays, rays_sensor)

@@ -656,6 +656,55 @@ class RenderBatchFn(torch.autograd.Function):
         return own.clone(), None, None, None, None
 
 
+class HostFrames:
+    """Frames of one sensor shape delivered to page-locked host memory with
+    `depth` frames in flight: each frame renders into its own device buffers on
+    a render stream (salf_render_rays), and the copy engine moves the previous
+    frame's outputs to the host on a copy stream meanwhile.  submit() returns a
+    slot; result(slot) waits for that frame and returns its host tensors, which
+    stay valid until the slot is submitted again (every `depth` frames)."""
+
+    def __init__(self, scene: Scene, sensor: dict, outputs=("rgb", "depth", "opacity"),
+                 depth: int = 2, t_min=1e-4, background=(0.0, 0.0, 0.0), want_intensity=False):
+        if depth < 1:
+            raise ValueError("depth must be >= 1")
+        self.scene, self.outputs, self.depth = scene, tuple(outputs), depth
+        self.kw = dict(t_min=t_min, background=background, want_intensity=want_intensity)
+        R = n_rays(sensor)
+        shape = lambda k: (R, 3) if k == "rgb" else (R,)
+        dev = scene.ctx.device
+        self.dev = [{k: torch.empty(shape(k), device=f"cuda:{dev}") for k in self.outputs}
+                    for _ in range(depth)]
+        self.host = [{k: torch.empty(shape(k), pin_memory=True) for k in self.outputs}
+                     for _ in range(depth)]
+        self.render_stream = torch.cuda.Stream(device=dev)
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.rendered = [torch.cuda.Event() for _ in range(depth)]
+        self.copied = [torch.cuda.Event() for _ in range(depth)]
+        self.used = [False] * depth
+        self.n = 0
+
+    def submit(self, sensor: dict) -> int:
+        b = self.n % self.depth
+        self.n += 1
+        if self.used[b]:  # the copy that last read these device buffers has run
+            self.render_stream.wait_event(self.copied[b])
+        self.scene.render(sensor, out=self.dev[b], outputs=self.outputs, valid=False,
+                          stream=self.render_stream, **self.kw)
+        self.rendered[b].record(self.render_stream)
+        self.copy_stream.wait_event(self.rendered[b])
+        with torch.cuda.stream(self.copy_stream):
+            for k in self.outputs:
+                self.host[b][k].copy_(self.dev[b][k], non_blocking=True)
+        self.copied[b].record(self.copy_stream)
+        self.used[b] = True
+        return b
+
+    def result(self, slot: int) -> dict:
+        self.copied[slot].synchronize()
+        return self.host[slot]
+
+
 class Server:
     """Continuous-batching render server (salf_serve_*)."""
 

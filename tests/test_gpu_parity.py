@@ -325,6 +325,35 @@ def test_async_pinned_host_outputs(salf):
     g.check()
 
 
+def test_host_frames_pipeline(salf):
+    """HostFrames: device renders with the copy engine moving each frame to
+    page-locked memory while the next renders; every frame equals its device
+    render bit for bit, including slots reused after `depth` frames."""
+    sc = synth.random_multilevel_scene(seed=11, max_level=2, dims=(6, 5, 4), p_occ=0.7)
+    g = salf.Scene(sc)
+    outs = ("rgb", "depth", "opacity")
+    cams = [synth.pinhole(200, 150, 75.0, synth.camera_pose_looking((-2.2, 0.4 + 0.15 * i, 1.1),
+                                                                     0.1 * i)) for i in range(5)]
+    refs = []
+    for cam in cams:
+        d = g.render(cam, outputs=outs)
+        torch.cuda.synchronize()
+        refs.append({k: d[k].cpu() for k in outs})
+    hf = salf.HostFrames(g, cams[0], outputs=outs, depth=2)
+    prev = None
+    for i, cam in enumerate(cams):
+        slot = hf.submit(cam)
+        if prev is not None:
+            got = hf.result(prev[1])
+            for k in outs:
+                assert torch.equal(got[k], refs[prev[0]][k]), (prev[0], k)
+        prev = (i, slot)
+    got = hf.result(prev[1])
+    for k in outs:
+        assert torch.equal(got[k], refs[prev[0]][k]), (prev[0], k)
+    g.check()
+
+
 def test_update_params_matches_rebuild(salf):
     sc = synth.random_multilevel_scene(seed=2, max_level=2)
     sen = synth.pinhole(40, 30, 75.0, synth.camera_pose_looking((-2.2, 0.6, 1.1), 0.15))
